@@ -1,0 +1,224 @@
+/*
+ * sfci.h -- C ABI of the GB300 sparse-FCI sigma = H psi library (libsfci.so).
+ *
+ * The method is Sparse Full Configuration Interaction (L. Wang, arXiv
+ * 2312.01846): a Lanczos-like solver whose basis vectors are truncated to the
+ * N_d largest-magnitude determinants (Sec. 2.1, Eqs. 10-11), built on a sparse
+ * Hamiltonian x sparse vector product whose intermediate elements are
+ * generated on the fly and merged by a consecutive-integer index of the
+ * determinants (Sec. 2.2, Eq. 12).
+ *
+ * Conventions used by every call:
+ *  - A determinant is a pair of spin strings (alpha, beta), each a uint64 with
+ *    bit p set when spatial orbital p (0-based) is occupied; n <= 64.
+ *  - A spin string's index is Eq. 12, h = sum_i C(chi_i - 1, i) with chi_i the
+ *    i-th occupied orbital counted from 1 (the colex rank).  A determinant's
+ *    index ("rank") is alpha-major: rank = h(alpha) * C(n, n_beta) + h(beta),
+ *    a bijection onto [0, dim), dim = C(n, n_alpha) C(n, n_beta) (Sec. 3 buckets
+ *    on the spin-up string only; alpha-major ranks make those buckets
+ *    contiguous rank ranges).
+ *  - A sparse vector is two arrays: uint64 rank[m] strictly ascending and
+ *    double coef[m] ("2-tuples (i, alpha_i)", Sec. 2.2).
+ *  - Integrals: h[p*n+q] = h_pq and g[((p*n+q)*n+r)*n+s] = (pq|rs) in
+ *    chemists' notation, real orbitals, 8-fold symmetric, float64, row-major.
+ *  - H = e_core + sum_pq h_pq sum_s a+_ps a_qs
+ *          + 1/2 sum_pqrs (pq|rs) sum_st a+_ps a+_rt a_st a_qs.
+ *    Determinants are ordered products of creators, alpha orbitals ascending
+ *    then beta ascending; that fixes the signs of sigma's entries.
+ *  - Pointers documented "device" must be CUDA device (or managed) memory on
+ *    the current device; "host" pointers are ordinary host memory.  `stream`
+ *    is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    All work of a call is ordered on that stream.
+ *  - Every call returns an sfci_status; none throws or aborts.  On failure
+ *    sfci_last_error() gives a thread-local message.  Calls that return a
+ *    count to the host synchronise `stream`.
+ *  - Ownership: the caller owns every vector, output and workspace buffer;
+ *    the library owns handles and the device copies of the integrals.
+ */
+#ifndef SFCI_H
+#define SFCI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sfci_status {
+    SFCI_OK = 0,
+    SFCI_E_INVALID = 1,  /* bad argument, unsorted input, rank >= dim, ...    */
+    SFCI_E_CAPACITY = 2, /* an output or workspace is too small; see the call */
+    SFCI_E_OVERFLOW = 3, /* n > 64 or dim does not fit below 2^64 - 1         */
+    SFCI_E_CUDA = 4,     /* a CUDA runtime call failed                         */
+    SFCI_E_TIMEOUT = 5,  /* a bounded device wait ran out                      */
+    SFCI_E_NOMEM = 6     /* device or host allocation failed                   */
+} sfci_status;
+
+/* Static, human-readable name of a status code. */
+const char *sfci_status_string(int status);
+/* Detail of the last failure on the calling thread ("" if none). */
+const char *sfci_last_error(void);
+/* Library version, major*10000 + minor*100 + patch. */
+int sfci_version(void);
+/* Number of CUDA kernels the library has launched in this process so far
+ * (a diagnostic: the difference across a region counts its launches). */
+int64_t sfci_kernel_launches(void);
+
+/* ------------------------------------------------------------- system */
+
+typedef struct sfci_system sfci_system; /* opaque */
+
+/* Copy the integrals (host pointers; h: n*n, g: n^4 float64) to the current
+ * device and build the binomial table C(b, m) used by Eq. 12.  n in [1, 64],
+ * 0 <= n_alpha, n_beta <= n.  Returns SFCI_E_OVERFLOW when dim >= 2^64 - 1,
+ * SFCI_E_INVALID for bad counts.  `flags` is reserved (pass 0). */
+sfci_status sfci_system_create(sfci_system **out, int n_orb, int n_alpha, int n_beta,
+                               const double *h_host, const double *g_host, double e_core,
+                               uint32_t flags);
+sfci_status sfci_system_destroy(sfci_system *sys);
+/* dim = C(n, n_alpha) C(n, n_beta). */
+sfci_status sfci_dim(const sfci_system *sys, uint64_t *dim);
+/* Determinants connected to one determinant by single and double
+ * excitations: na va + nb vb + C(na,2)C(va,2) + C(nb,2)C(vb,2) + na va nb vb
+ * (v = n - n_electrons).  Intermediate elements per input entry = this + 1. */
+sfci_status sfci_n_connected(const sfci_system *sys, int64_t *n_conn);
+
+/* ---------------------------------------------------------- Eq. 12 */
+
+/* rank[i] = alpha-major index of (alpha[i], beta[i])  (Eq. 12).  Device
+ * pointers, count entries.  SFCI_E_INVALID if any string has the wrong
+ * electron count or bits at or above n (those ranks are set to UINT64_MAX).
+ * Synchronises the stream. */
+sfci_status sfci_rank(const sfci_system *sys, const uint64_t *alpha, const uint64_t *beta,
+                      uint64_t *rank, int64_t count, void *stream);
+/* Inverse of sfci_rank (greedy inverse of Eq. 12).  SFCI_E_INVALID if some
+ * rank >= dim (those strings are set to 0).  Synchronises the stream. */
+sfci_status sfci_unrank(const sfci_system *sys, const uint64_t *rank, uint64_t *alpha,
+                        uint64_t *beta, int64_t count, void *stream);
+
+/* ---------------------------------------------------------- sigma = H psi */
+
+/* Workspace (bytes, device) that sfci_sigma needs for n_in input entries and
+ * room for out_cap output entries.  It holds an open-addressing table of
+ * 2^ceil(log2(2 out_cap)) slots (at least 1024) plus sort buffers. */
+sfci_status sfci_sigma_workspace_bytes(const sfci_system *sys, int64_t n_in, int64_t out_cap,
+                                       size_t *bytes);
+
+/* sigma = H psi (Sec. 2.2).  For every input entry (D, c_D) the library
+ * enumerates D and all its single and double excitations D', evaluates the
+ * Slater-Condon element <D'|H|D>, and adds the intermediate element
+ * <D'|H|D> c_D into the entry of rank(D'); exactly-zero products are not
+ * generated.  Entries that received at least one non-zero element and whose
+ * |sum| >= eps_screen (eps_screen <= 0: no screen; the paper's epsilon of
+ * Sec. 3) are written to out_rank/out_coef (device) ascending by rank, and
+ * their count to *n_out (host).
+ * in_rank/in_coef: device, n_in entries, ranks strictly ascending and < dim.
+ * Returns SFCI_E_CAPACITY if more than out_cap entries result: then *n_out is
+ * the exact count when it is at most the table's slot count, otherwise a lower
+ * bound (retry with a larger out_cap).  SFCI_E_CAPACITY also when ws_bytes is
+ * below sfci_sigma_workspace_bytes.  No allocation; synchronises the stream.
+ * Summation order inside an entry is not fixed (atomic adds), so results agree
+ * with an ordered sum to rounding. */
+sfci_status sfci_sigma(const sfci_system *sys, const uint64_t *in_rank, const double *in_coef,
+                       int64_t n_in, double eps_screen, uint64_t *out_rank, double *out_coef,
+                       int64_t out_cap, int64_t *n_out, void *workspace, size_t ws_bytes,
+                       void *stream);
+
+/* ---------------------------------------------------------- Eq. 11 */
+
+sfci_status sfci_truncate_topk_workspace_bytes(int64_t n, int64_t k, size_t *bytes);
+
+/* Truncation of Eq. 11: keep the min(k, #non-zero) entries of largest |coef|;
+ * among equal |coef| the smaller rank wins; exact zeros are never kept.  With
+ * normalize != 0 the kept coefficients are divided by their 2-norm
+ * sqrt(sum c^2).  rank/coef: device, n entries, ranks unique (any order).
+ * Output (device, room for k entries) ascending by rank; *n_out (host) = kept
+ * count.  Selection is exact: decided on the bit patterns of |coef| and rank.
+ * No allocation; synchronises the stream. */
+sfci_status sfci_truncate_topk(const uint64_t *rank, const double *coef, int64_t n, int64_t k,
+                               int normalize, uint64_t *out_rank, double *out_coef,
+                               int64_t *n_out, void *workspace, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------- SFCI Lanczos */
+
+typedef struct sfci_params {
+    int64_t n_keep;         /* N_d: entries kept per basis vector (Eq. 11)          */
+    int64_t table_capacity; /* slots of sigma's hash table; 0 = sized automatically */
+    double eps_screen;      /* drop |sigma_k| < eps_screen before the dots (Sec. 3) */
+    double conv_tol;        /* halt when E(n-1) - E(n) < conv_tol (Sec. 2.1); <= 0 off */
+    int32_t n_lanczos;      /* N_L: basis vectors per cycle, w_0 included (Sec. 2.1) */
+    int32_t max_iter;       /* the step that reaches this sigma count ends its cycle; <= 0 off */
+    uint32_t flags;         /* reserved, pass 0                                      */
+    int32_t reserved;
+} sfci_params;
+
+typedef struct sfci_step_info {
+    int32_t iter;      /* sigma applications so far, this one included (N_I)        */
+    int32_t cycle;     /* cycle (restart) index of this step                        */
+    int32_t index;     /* i: position of this step's input w_i within its cycle     */
+    int32_t cycle_end; /* 1: this step solved T x = lambda S x and restarted        */
+    int32_t converged; /* 1: the halting test passed at this cycle end              */
+    int32_t breakdown; /* 1: u vanished (||u|| < 1e-14 |a_i|) and the cycle ended     */
+    double lambda_min; /* lowest root of T x = lambda S x (valid when cycle_end)    */
+    double a;          /* a_i = <w_i|sigma_i>                                       */
+    double b;          /* b_i = <w_{i-1}|sigma_i> (0 for i = 0)                      */
+    double u_norm;     /* ||u_{i+1}|| before truncation (0 at a cycle end)          */
+    double t00;        /* <w_0|H|w_0> of this cycle                                 */
+    int64_t n_in;      /* entries of w_i                                            */
+    int64_t n_sigma;   /* entries of sigma_i after the screen                       */
+    int64_t n_kept;    /* entries of the next basis vector                          */
+    int64_t n_elements;/* intermediate elements enumerated for sigma_i              */
+    int64_t n_psi;     /* non-zero entries of Psi = sum_j x_j w_j (cycle end)         */
+    double ms_sigma;   /* device time of the sigma stage (CUDA events)              */
+    double ms_step;    /* device time of the whole step                             */
+} sfci_step_info;
+
+typedef struct sfci_lanczos sfci_lanczos; /* opaque; owns w_0..w_{N_L-1}, T, S, table */
+
+/* Start a solver from a trial vector (device pointers, ranks strictly
+ * ascending; the paper starts from one determinant, Sec. 3).  The trial
+ * vector is truncated to n_keep and normalised to become w_0.  Allocates the
+ * solver's device memory; the system must outlive the solver. */
+sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
+                                const sfci_params *params, const uint64_t *init_rank,
+                                const double *init_coef, int64_t n_init, void *stream);
+/* One sigma application (one of the paper's N_I iterations):
+ *   sigma_i = H w_i (screened); T_ji = <w_j|sigma_i>, S_ji = <w_j|w_i> for j <= i;
+ *   then either w_{i+1} = normalise(top_{N_d}(sigma_i - a_i w_i - b_i w_{i-1}))
+ *   (Eqs. 10-11), or, at the cycle's last vector, the lowest root of
+ *   T x = lambda S x, Psi = sum_j x_j w_j, and w_0 = normalise(top_{N_d}(Psi)).
+ * info (host) receives the step's scalars.  Synchronises the solver's stream.
+ * SFCI_E_CAPACITY only if sigma's table cannot grow in device memory. */
+sfci_status sfci_lanczos_step(sfci_lanczos *lz, sfci_step_info *info);
+/* Restart the solver from a new trial vector (device pointers, ranks strictly
+ * ascending): it is truncated to n_keep and normalised into w_0, and a new
+ * cycle begins (T, S and the halting history are cleared).  Lets a caller
+ * stream vectors through the solver without re-creating it. */
+sfci_status sfci_lanczos_load(sfci_lanczos *lz, const uint64_t *rank, const double *coef,
+                              int64_t n);
+/* Copy the current input vector (the w_i the next step will use) to device
+ * buffers with room for cap entries; *n (host) = its length. */
+sfci_status sfci_lanczos_vector(const sfci_lanczos *lz, uint64_t *rank, double *coef,
+                                int64_t cap, int64_t *n);
+/* T and S of the current cycle so far (host, n_lanczos^2 each, row-major,
+ * upper triangle j <= i filled). */
+sfci_status sfci_lanczos_matrices(const sfci_lanczos *lz, double *T, double *S);
+sfci_status sfci_lanczos_destroy(sfci_lanczos *lz);
+
+/* ---------------------------------------------------------- test exports */
+
+/* Every intermediate element of the given entries, unscaled: for input entry
+ * s (device rank[s]) and each of its n_conn + 1 targets D' (D itself first),
+ * src[s*(n_conn+1)+e] = s, tgt[...] = rank(D'), elem[...] = <D'|H|D>.
+ * Device outputs with room for cap entries; *n_out (host) = n*(n_conn+1).
+ * Synchronises the stream. */
+sfci_status sfci_debug_excitations(const sfci_system *sys, const uint64_t *rank, int64_t n,
+                                   int64_t *src, uint64_t *tgt, double *elem, int64_t cap,
+                                   int64_t *n_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFCI_H */

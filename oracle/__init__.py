@@ -74,6 +74,8 @@ def lib():
         L.or_hmat.restype = C.c_double
         L.or_hmat.argtypes = [C.POINTER(_Sys), C.c_uint64, C.c_uint64, C.c_uint64,
                               C.c_uint64]
+        L.or_hmat_batch.restype = None
+        L.or_hmat_batch.argtypes = [C.POINTER(_Sys), _u64p, _u64p, _u64p, _u64p, _f64p, C.c_int64]
         L.or_n_connected.restype = C.c_int64
         L.or_n_connected.argtypes = [C.c_int, C.c_int, C.c_int]
         L.or_connected.restype = C.c_int64
@@ -186,6 +188,14 @@ def connected(n, na, nb, alpha, beta):
 def hmat(sys: System, src, tgt):
     """<tgt|H|src> with src = (alpha, beta), tgt = (alpha, beta)."""
     return float(lib().or_hmat(sys.ref, int(src[0]), int(src[1]), int(tgt[0]), int(tgt[1])))
+
+
+def hmat_batch(sys: System, src_a, src_b, tgt_a, tgt_b):
+    """<tgt|H|src> for arrays of determinants."""
+    a = [np.ascontiguousarray(x, dtype=np.uint64) for x in (src_a, src_b, tgt_a, tgt_b)]
+    out = np.empty(a[0].size)
+    lib().or_hmat_batch(sys.ref, *[_p(x, _u64p) for x in a], _p(out, _f64p), a[0].size)
+    return out
 
 
 def dense_h(sys: System):

@@ -307,6 +307,14 @@ double or_hmat(const or_sys *S, uint64_t as, uint64_t bs, uint64_t at, uint64_t 
     }
 }
 
+void or_hmat_batch(const or_sys *S, const uint64_t *as, const uint64_t *bs, const uint64_t *at,
+                   const uint64_t *bt, double *out, int64_t count)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < count; i++)
+        out[i] = or_hmat(S, as[i], bs[i], at[i], bt[i]);
+}
+
 /* ---------------------------------------------------------- enumeration */
 
 /* Number of determinants connected to one determinant by a single or double

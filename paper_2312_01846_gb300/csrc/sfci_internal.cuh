@@ -1,0 +1,242 @@
+// Internal declarations shared by the translation units of libsfci.so.
+//
+// Data layout on the device (one GPU, HBM3e):
+//  * a sparse vector is SoA: uint64 rank[m] ascending, double coef[m];
+//  * sigma's intermediate elements are merged in an open-addressing hash table
+//    of 16-byte slots {uint64 key, double val} (key = rank, kEmpty = free);
+//    the key and the value share one 32-byte sector, so a hit costs one
+//    sector;
+//  * the integrals stay in HBM (g is n^4 doubles: 4.9 MB at n = 28, resident
+//    in the 129 MB L2) and are read through the read-only path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sfci.h"
+
+namespace sfci {
+
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxProbe = 1 << 16;  // linear-probe bound; beyond it the table is "full"
+
+struct Slot {
+    unsigned long long key;
+    double val;
+};
+
+// The hash table as the kernels see it.
+struct Table {
+    Slot *slots;
+    unsigned long long mask;  // capacity - 1 (capacity a power of two)
+    int shift;                // 64 - log2(capacity)
+    int *status;              // device: bit 0 = a probe ran past kMaxProbe
+    unsigned long long *count;  // device: keys inserted
+};
+
+// Read-only description of a system for the kernels.
+struct SysDev {
+    int n, na, nb, va, vb;
+    int ks;              // row stride of the binomial table: max(na, nb) + 3
+    int sa, sb;          // singles per spin: na*va, nb*vb
+    int po_a, pv_a, po_b, pv_b;  // pair counts C(na,2), C(va,2), C(nb,2), C(vb,2)
+    int pair_off[4];     // offsets (in pairs) of the four pair lists
+    int n_pairs;         // total pairs
+    unsigned long long ca, cb, dim;
+    long long n_conn;    // connected determinants per determinant
+    double e_core;
+    const double *h;     // n*n
+    const double *g;     // n^4
+    const unsigned long long *binom;  // [(n+1) * ks]: C(b, m)
+    const unsigned char *pairs;       // 2 bytes per pair: (first, second) positions, first < second
+};
+
+}  // namespace sfci
+
+struct sfci_system {
+    sfci::SysDev d;
+    void *dev_block;  // one allocation holding h, g, binom, pairs
+    int *dev_status;  // scratch status words for rank/unrank
+    int device;
+};
+
+namespace sfci {
+
+// ------------------------------------------------------------- launch count
+// every kernel launch of the library increments this host counter
+void count_launch();
+long long launch_count();
+
+// ------------------------------------------------------------- error text
+void set_error(const std::string &msg);
+sfci_status cuda_fail(cudaError_t e, const char *what);
+#define SFCI_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return sfci::cuda_fail(e_, #call); \
+    } while (0)
+
+// ------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ int parity64(unsigned long long x) { return __popcll(x) & 1; }
+
+// bits strictly between orbitals x and y
+__device__ __forceinline__ unsigned long long between_mask(int x, int y) {
+    int lo = x < y ? x : y, hi = x < y ? y : x;
+    return ((1ull << hi) - 1ull) & ~((2ull << lo) - 1ull);
+}
+
+// Eq. 12 on the device: h = sum over occupied orbitals b (0-based, ascending)
+// of C(b, m), m the electron's 1-based position; bt = binomial table in smem.
+__device__ __forceinline__ unsigned long long string_rank(unsigned long long s,
+                                                          const unsigned long long *bt,
+                                                          int ks) {
+    unsigned long long h = 0;
+    int m = 1;
+    while (s) {
+        int b = __ffsll((long long)s) - 1;
+        h += bt[b * ks + m];
+        ++m;
+        s &= s - 1ull;
+    }
+    return h;
+}
+
+// Greedy inverse of Eq. 12, one warp: for i = m..1 the largest c <= top with
+// C(c, i) <= r.  C(c, i) is non-decreasing in c, so the lanes testing
+// c = lane and c = lane + 32 give a prefix; its last lane is c.
+__device__ __forceinline__ unsigned long long string_unrank_warp(unsigned long long r, int n,
+                                                                 int m,
+                                                                 const unsigned long long *bt,
+                                                                 int ks) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long s = 0;
+    int top = n - 1;
+    for (int i = m; i >= 1; --i) {
+        int c0 = lane, c1 = lane + 32;
+        bool p0 = (c0 <= top) && bt[c0 * ks + i] <= r;
+        bool p1 = (c1 <= top) && bt[c1 * ks + i] <= r;
+        unsigned b0 = __ballot_sync(kFull, p0), b1 = __ballot_sync(kFull, p1);
+        int c = b1 ? 63 - __clz(b1) : 31 - __clz(b0);
+        s |= 1ull << c;
+        r -= bt[c * ks + i];
+        top = c - 1;
+    }
+    return s;
+}
+
+__device__ __forceinline__ unsigned long long hash_slot(unsigned long long key, int shift) {
+    return (key * 0x9E3779B97F4A7C15ull) >> shift;
+}
+
+// Add v into the entry `key`, inserting the key if absent (linear probing).
+__device__ __forceinline__ bool table_add(const Table &t, unsigned long long key, double v,
+                                          unsigned &inserted) {
+    unsigned long long h = hash_slot(key, t.shift);
+    for (int probe = 0; probe < kMaxProbe; ++probe) {
+        Slot *s = t.slots + h;
+        unsigned long long cur = __ldcg(&s->key);
+        if (cur == key) {
+            atomicAdd(&s->val, v);
+            return true;
+        }
+        if (cur == kEmpty) {
+            unsigned long long old = atomicCAS(&s->key, kEmpty, key);
+            if (old == kEmpty || old == key) {
+                inserted += (old == kEmpty);
+                atomicAdd(&s->val, v);
+                return true;
+            }
+        }
+        h = (h + 1ull) & t.mask;
+    }
+    atomicOr(t.status, 1);
+    return false;
+}
+
+// Find `key`; returns the slot index or -1.
+__device__ __forceinline__ long long table_find(const Table &t, unsigned long long key) {
+    unsigned long long h = hash_slot(key, t.shift);
+    for (int probe = 0; probe < kMaxProbe; ++probe) {
+        unsigned long long cur = __ldcg(&t.slots[h].key);
+        if (cur == key) return (long long)h;
+        if (cur == kEmpty) return -1;
+        h = (h + 1ull) & t.mask;
+    }
+    return -1;
+}
+
+// ------------------------------------------------------------- launchers
+// (defined in the .cu files; all enqueue on `st` and do not synchronise)
+
+// sfci_emit.cu
+size_t emit_smem_bytes(const SysDev &d, int warps);
+cudaError_t launch_emit(const SysDev &d, const unsigned long long *in_rank,
+                        const double *in_coef, long long n_in, Table t, cudaStream_t st);
+cudaError_t launch_debug_excitations(const SysDev &d, const unsigned long long *in_rank,
+                                     long long n_in, long long *src, unsigned long long *tgt,
+                                     double *elem, cudaStream_t st);
+cudaError_t launch_rank(const SysDev &d, const unsigned long long *a, const unsigned long long *b,
+                        unsigned long long *r, long long count, int *status, cudaStream_t st);
+cudaError_t launch_unrank(const SysDev &d, const unsigned long long *r, unsigned long long *a,
+                          unsigned long long *b, long long count, int *status, cudaStream_t st);
+
+// sfci_table.cu
+cudaError_t table_clear(Table t, cudaStream_t st);
+// mark entries with |val| < eps as screened (-0.0)
+cudaError_t table_screen(Table t, double eps, unsigned long long *screened_dev, cudaStream_t st);
+// flag[0] |= 1 if rank is not strictly ascending or some rank >= dim
+cudaError_t validate_sorted(const unsigned long long *rank, long long n, unsigned long long dim,
+                            int *flag, cudaStream_t st);
+// add sign * scale[0] * coef[k] into entry rank[k] (scale device pointer, or
+// host constant when scale == nullptr: then value = sign * hscale * coef)
+cudaError_t table_axpy(Table t, const unsigned long long *rank, const double *coef, long long m,
+                       const double *scale, double hscale, double sign, cudaStream_t st);
+// unordered extraction of live entries with !(|val| < eps) into out; count in *n_dev
+cudaError_t table_extract(Table t, double eps, unsigned long long *out_rank, double *out_val,
+                          long long cap, unsigned long long *n_dev, cudaStream_t st);
+// dots: out[j] = sum_k w_j[k] * sigma[w_j.rank[k]] for j < nvec (partials workspace)
+struct VecRef {
+    const unsigned long long *rank;
+    const double *coef;
+    long long n;
+};
+constexpr int kMaxVec = 64;
+size_t dots_workspace_bytes(int nvec, long long max_n);
+cudaError_t table_dots(Table t, const VecRef *vecs_host, int nvec, double *out_dev,
+                       void *ws, cudaStream_t st);
+// S: out[j] = <w_j | w_last> by binary search of w_last entries in w_j
+cudaError_t vec_overlaps(const VecRef *vecs_host, int nvec, VecRef last, double *out_dev,
+                         void *ws, cudaStream_t st);
+
+// sfci_select.cu
+size_t select_workspace_bytes(long long n_items, long long k);
+// Generic source of (key, val) items: either SoA arrays (stride 1) or table
+// slots (stride 2, keys == kEmpty skipped).
+struct Items {
+    const unsigned long long *key;
+    const double *val;
+    int stride;
+    long long n;
+};
+// top-k by (|val| desc, key asc), non-zero only; writes up to k entries sorted
+// (unordered) to out; count to *n_out_dev.  If sumsq_dev != nullptr it
+// receives sum val^2 over all valid items, and total_dev their number.
+cudaError_t select_topk(Items it, long long k, unsigned long long *out_key, double *out_val,
+                        unsigned long long *n_out_dev, double *sumsq_dev,
+                        unsigned long long *total_dev, void *ws, size_t ws_bytes, cudaStream_t st);
+size_t sort_workspace_bytes(long long n);
+// stable LSD radix sort of (key, val) by key on the low `bits` bits; result in
+// key/val (uses ws as ping-pong buffers); n read from the device when n_dev
+size_t sort_pairs_bytes(long long cap);
+cudaError_t sort_pairs(unsigned long long *key, double *val, long long cap,
+                       const unsigned long long *n_dev, int bits, void *ws, cudaStream_t st);
+// c[i] /= sqrt(sum c^2) over n (device count) entries, deterministic order
+cudaError_t normalize_vec(double *val, long long cap, const unsigned long long *n_dev,
+                          void *ws, cudaStream_t st);
+size_t normalize_ws_bytes(long long cap);
+
+}  // namespace sfci
