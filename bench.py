@@ -53,6 +53,8 @@ def parse():
                    help="input determinants in the CPU oracle's timed sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--table-capacity", type=int, default=0,
+                   help="merge-table slots (0 = sized by the solver)")
     return p.parse_args()
 
 
@@ -217,7 +219,7 @@ def run_ours(a):
     gsys = sf.System.from_dict(d)
     stream = torch.cuda.current_stream()
     lz = sf.Lanczos(gsys, np.array([0], dtype=np.uint64), np.array([1.0]), a.nkeep, a.nlanczos,
-                    stream=stream)
+                    table_capacity=a.table_capacity, stream=stream)
     for _ in range(a.warmup):
         lz.step()
     barrier()

@@ -206,6 +206,28 @@ sfci_status sfci_lanczos_vector(const sfci_lanczos *lz, uint64_t *rank, double *
 sfci_status sfci_lanczos_matrices(const sfci_lanczos *lz, double *T, double *S);
 sfci_status sfci_lanczos_destroy(sfci_lanczos *lz);
 
+/* ---------------------------------------------------------- density matrices */
+
+/* Workspace (bytes, device) for sfci_rdm12 on a vector of n entries. */
+sfci_status sfci_rdm12_workspace_bytes(const sfci_system *sys, int64_t n, size_t *bytes);
+
+/* Spin-summed one- and two-particle density matrices of psi (not normalised),
+ * produced by the sigma excitation generator (every D' in {D} and the single
+ * and double excitations of D that psi holds):
+ *   rdm1[p*n+q]             = sum_s   <psi| a+_ps a_qs |psi>
+ *   rdm2[((p*n+q)*n+r)*n+s] = sum_st  <psi| a+_ps a+_rt a_st a_qs |psi>
+ * so that <psi|H|psi> = e_core <psi|psi> + sum h rdm1 + 1/2 sum (pq|rs) rdm2, and
+ * for fixed psi dE/dh = rdm1 / <psi|psi>, dE/d(pq|rs) = rdm2 / (2 <psi|psi>).
+ * These gradients of the Rayleigh energy are the adjoint the paper does not
+ * have (its method stops at the energy, Sec. 2.1).
+ * rank/coef: device, n entries, ranks strictly ascending and < dim.  rdm1
+ * (n^2) and rdm2 (n^4) are device float64 outputs (overwritten); *norm2 (host,
+ * may be NULL) receives <psi|psi>.  Accumulates with atomic adds (rounding order
+ * not fixed).  No allocation; synchronises the stream. */
+sfci_status sfci_rdm12(const sfci_system *sys, const uint64_t *rank, const double *coef, int64_t n,
+                       double *rdm1, double *rdm2, double *norm2, void *workspace,
+                       size_t ws_bytes, void *stream);
+
 /* ---------------------------------------------------------- test exports */
 
 /* Every intermediate element of the given entries, unscaled: for input entry

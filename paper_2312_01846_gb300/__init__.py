@@ -84,6 +84,8 @@ def lib():
         "sfci_lanczos_vector": (_i32, [_vp, _vp, _vp, _i64, C.POINTER(_i64)]),
         "sfci_lanczos_matrices": (_i32, [_vp, _vp, _vp]),
         "sfci_lanczos_destroy": (_i32, [_vp]),
+        "sfci_rdm12_workspace_bytes": (_i32, [_vp, _i64, C.POINTER(C.c_size_t)]),
+        "sfci_rdm12": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, C.POINTER(_f64), _vp, C.c_size_t, _vp]),
         "sfci_debug_excitations": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, C.POINTER(_i64), _vp]),
     }
     for name, (res, args) in sig.items():
@@ -184,21 +186,26 @@ def sigma_workspace_bytes(sys: System, n_in, out_cap):
 
 
 def sfci_sigma(sys: System, rank, coef, eps_screen=0.0, out_cap=None, stream=None):
-    """sigma = H psi; returns (rank, coef) ascending by rank.  Grows the output
-    once if the first guess of its size was too small."""
+    """sigma = H psi; returns (rank, coef) ascending by rank.  If out_cap is not
+    given it starts from min(n_in * (n_conn + 1), 2^24) and grows on
+    SFCI_E_CAPACITY."""
     r = _dev(rank, torch.int64)
     c = _dev(coef, torch.float64)
-    cap = int(out_cap) if out_cap is not None else max(1024, 64 * r.numel())
-    for _ in range(4):
+    if out_cap is not None:
+        cap = int(out_cap)
+    else:
+        cap = max(1024, min(r.numel() * (sys.n_conn + 1), 1 << 24))
+    for _ in range(16):
         ws = torch.empty(sigma_workspace_bytes(sys, r.numel(), cap), dtype=torch.uint8, device="cuda")
-        orank = torch.empty(cap, dtype=torch.int64, device="cuda")
-        ocoef = torch.empty(cap, dtype=torch.float64, device="cuda")
+        orank = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
+        ocoef = torch.empty(max(cap, 1), dtype=torch.float64, device="cuda")
         n = C.c_int64()
         st = lib().sfci_sigma(sys.handle, _ptr(r), _ptr(c), r.numel(), float(eps_screen),
                               _ptr(orank), _ptr(ocoef), cap, C.byref(n), _ptr(ws), ws.numel(),
                               _stream(stream))
         if st == SFCI_E_CAPACITY and n.value > cap:
-            cap = int(n.value * 1.25) + 1024
+            del ws, orank, ocoef
+            cap = max(int(n.value * 1.25) + 1024, 4 * cap)
             continue
         _check(st, "sfci_sigma")
         return orank[: n.value], ocoef[: n.value]
@@ -233,6 +240,44 @@ def sfci_debug_excitations(sys: System, rank, stream=None):
                                         _ptr(elem), m, C.byref(n), _stream(stream)),
            "sfci_debug_excitations")
     return src[:m], tgt[:m], elem[:m]
+
+
+def sfci_rdm12(sys: System, rank, coef, stream=None):
+    """Spin-summed 1- and 2-RDMs of psi (not normalised) and <psi|psi>."""
+    r = _dev(rank, torch.int64)
+    c = _dev(coef, torch.float64)
+    nb = C.c_size_t()
+    _check(lib().sfci_rdm12_workspace_bytes(sys.handle, r.numel(), C.byref(nb)),
+           "sfci_rdm12_workspace_bytes")
+    ws = torch.empty(int(nb.value), dtype=torch.uint8, device="cuda")
+    n = sys.n
+    g1 = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    g2 = torch.empty((n, n, n, n), dtype=torch.float64, device="cuda")
+    nrm = C.c_double()
+    _check(lib().sfci_rdm12(sys.handle, _ptr(r), _ptr(c), r.numel(), _ptr(g1), _ptr(g2),
+                            C.byref(nrm), _ptr(ws), ws.numel(), _stream(stream)), "sfci_rdm12")
+    return g1, g2, float(nrm.value)
+
+
+class RayleighEnergy(torch.autograd.Function):
+    """E(h, g) = e_core + (sum h gamma + 1/2 sum g Gamma) / <psi|psi> for a fixed
+    sparse psi; gamma, Gamma come from sfci_rdm12, so dE/dh = gamma / <psi|psi>
+    and dE/dg = Gamma / (2 <psi|psi>).  h: (n, n), g: (n, n, n, n) float64 CUDA
+    tensors; sys fixes n and the electron counts."""
+
+    @staticmethod
+    def forward(ctx, h, g, sys, rank, coef, e_core=0.0):
+        g1, g2, nrm = sfci_rdm12(sys, rank, coef)
+        d1 = g1 / nrm
+        d2 = g2 * (0.5 / nrm)
+        ctx.save_for_backward(d1, d2)
+        e = (h.to(d1) * d1).sum() + (g.to(d2) * d2).sum() + e_core
+        return e
+
+    @staticmethod
+    def backward(ctx, grad):
+        d1, d2 = ctx.saved_tensors
+        return grad * d1, grad * d2, None, None, None, None
 
 
 class Lanczos:

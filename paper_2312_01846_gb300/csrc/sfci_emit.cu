@@ -134,24 +134,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
         const unsigned long long beta = string_unrank_warp(hB, n, d.nb, bt, ks);
         const long long base = s * per;
 
-        // occupied / empty lists (ascending orbitals)
-        {
-            int seen_oa = 0, seen_va = 0, seen_ob = 0, seen_vb = 0;
-            const unsigned lt = (1u << lane) - 1u;
-            for (int half = 0; half < 2; ++half) {
-                const int p = lane + 32 * half;
-                const bool in = p < n;
-                const bool oa = in && ((alpha >> p) & 1ull), ob = in && ((beta >> p) & 1ull);
-                const unsigned moa = __ballot_sync(kFull, oa), mva = __ballot_sync(kFull, in && !oa);
-                const unsigned mob = __ballot_sync(kFull, ob), mvb = __ballot_sync(kFull, in && !ob);
-                if (oa) occA[seen_oa + __popc(moa & lt)] = (unsigned char)p;
-                else if (in) virA[seen_va + __popc(mva & lt)] = (unsigned char)p;
-                if (ob) occB[seen_ob + __popc(mob & lt)] = (unsigned char)p;
-                else if (in) virB[seen_vb + __popc(mvb & lt)] = (unsigned char)p;
-                seen_oa += __popc(moa), seen_va += __popc(mva);
-                seen_ob += __popc(mob), seen_vb += __popc(mvb);
-            }
-        }
+        build_lists(alpha, beta, n, occA, virA, occB, virB);
         __syncwarp();
         // single-excitation tables
         for (int x = lane; x < d.sa; x += 32) {

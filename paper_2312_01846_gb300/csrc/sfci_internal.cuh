@@ -21,7 +21,7 @@ namespace sfci {
 
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxProbe = 1 << 16;  // linear-probe bound; beyond it the table is "full"
+constexpr int kMaxProbe = 1 << 12;  // linear-probe bound; beyond it the table is "full"
 
 struct Slot {
     unsigned long long key;
@@ -128,6 +128,29 @@ __device__ __forceinline__ unsigned long long string_unrank_warp(unsigned long l
     return s;
 }
 
+// Occupied / empty orbital lists (ascending) of two spin strings from warp
+// ballots; every lane of the warp must call it.
+__device__ __forceinline__ void build_lists(unsigned long long alpha, unsigned long long beta, int n,
+                                            unsigned char *occA, unsigned char *virA,
+                                            unsigned char *occB, unsigned char *virB) {
+    const int lane = threadIdx.x & 31;
+    int seen_oa = 0, seen_va = 0, seen_ob = 0, seen_vb = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int half = 0; half < 2; ++half) {
+        const int p = lane + 32 * half;
+        const bool in = p < n;
+        const bool oa = in && ((alpha >> p) & 1ull), ob = in && ((beta >> p) & 1ull);
+        const unsigned moa = __ballot_sync(kFull, oa), mva = __ballot_sync(kFull, in && !oa);
+        const unsigned mob = __ballot_sync(kFull, ob), mvb = __ballot_sync(kFull, in && !ob);
+        if (oa) occA[seen_oa + __popc(moa & lt)] = (unsigned char)p;
+        else if (in) virA[seen_va + __popc(mva & lt)] = (unsigned char)p;
+        if (ob) occB[seen_ob + __popc(mob & lt)] = (unsigned char)p;
+        else if (in) virB[seen_vb + __popc(mvb & lt)] = (unsigned char)p;
+        seen_oa += __popc(moa), seen_va += __popc(mva);
+        seen_ob += __popc(mob), seen_vb += __popc(mvb);
+    }
+}
+
 __device__ __forceinline__ unsigned long long hash_slot(unsigned long long key, int shift) {
     return (key * 0x9E3779B97F4A7C15ull) >> shift;
 }
@@ -137,6 +160,8 @@ __device__ __forceinline__ bool table_add(const Table &t, unsigned long long key
                                           unsigned &inserted) {
     unsigned long long h = hash_slot(key, t.shift);
     for (int probe = 0; probe < kMaxProbe; ++probe) {
+        // a table already marked full fails fast instead of probing on
+        if ((probe & 255) == 255 && *(volatile int *)t.status) return false;
         Slot *s = t.slots + h;
         unsigned long long cur = __ldcg(&s->key);
         if (cur == key) {
