@@ -194,6 +194,40 @@ __device__ __forceinline__ long long table_find(const Table &t, unsigned long lo
     return -1;
 }
 
+// ------------------------------------------------------------- emit sinks
+// Where the emit kernel sends each intermediate element.
+enum EmitMode { kModeTable = 0, kModeDebug = 1, kModeBucket = 2 };
+
+// Bucketed merge: an element of rank k goes to bucket mix(k) >> (64 - log2B);
+// this pass keeps buckets [lo, hi).  Bucket b's elements fill
+// elem[(b - lo) * cap ...] up to cap; the rest go to an overflow list.
+struct BucketOut {
+    unsigned *count;          // [B] elements that arrived per bucket (all passes share it)
+    Slot *elem;               // [(hi - lo) * cap]
+    Slot *ovf;                // [ovf_cap]
+    unsigned long long *ovf_n;
+    long long ovf_cap;
+    int log2B;
+    unsigned lo, hi, cap;
+    int *status;              // bit 1: overflow list full
+};
+
+struct EmitOut {
+    Table t;                  // kModeTable
+    BucketOut b;              // kModeBucket
+    long long *dsrc;          // kModeDebug
+    unsigned long long *dtgt;
+    double *delem;
+};
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long key) {
+    return key * 0x9E3779B97F4A7C15ull;
+}
+
+__device__ __forceinline__ unsigned bucket_of(unsigned long long key, int log2B) {
+    return log2B > 0 ? (unsigned)(mix64(key) >> (64 - log2B)) : 0u;
+}
+
 // ------------------------------------------------------------- launchers
 // (defined in the .cu files; all enqueue on `st` and do not synchronise)
 
@@ -201,6 +235,9 @@ __device__ __forceinline__ long long table_find(const Table &t, unsigned long lo
 size_t emit_smem_bytes(const SysDev &d, int warps);
 cudaError_t launch_emit(const SysDev &d, const unsigned long long *in_rank,
                         const double *in_coef, long long n_in, Table t, cudaStream_t st);
+cudaError_t launch_emit_buckets(const SysDev &d, const unsigned long long *in_rank,
+                                const double *in_coef, long long n_in, const BucketOut &b,
+                                cudaStream_t st);
 cudaError_t launch_debug_excitations(const SysDev &d, const unsigned long long *in_rank,
                                      long long n_in, long long *src, unsigned long long *tgt,
                                      double *elem, cudaStream_t st);
