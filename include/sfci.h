@@ -150,7 +150,7 @@ typedef struct sfci_params {
     int32_t n_lanczos;      /* N_L: basis vectors per cycle, w_0 included (Sec. 2.1) */
     int32_t max_iter;       /* the step that reaches this sigma count ends its cycle; <= 0 off */
     uint32_t flags;         /* reserved, pass 0                                      */
-    int32_t reserved;
+    int32_t bucket_elems;   /* intermediate elements per merge bucket; 0 = automatic */
 } sfci_params;
 
 typedef struct sfci_step_info {
@@ -172,6 +172,8 @@ typedef struct sfci_step_info {
     int64_t n_psi;     /* non-zero entries of Psi = sum_j x_j w_j (cycle end)         */
     double ms_sigma;   /* device time of the sigma stage (CUDA events)              */
     double ms_step;    /* device time of the whole step                             */
+    double ms_emit;    /* of ms_sigma: the emit kernel (all passes)                 */
+    double ms_merge;   /* of ms_sigma: overflow sort + merge kernel (all passes)    */
 } sfci_step_info;
 
 typedef struct sfci_lanczos sfci_lanczos; /* opaque; owns w_0..w_{N_L-1}, T, S, table */

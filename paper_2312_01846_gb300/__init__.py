@@ -32,7 +32,7 @@ class Params(C.Structure):
     _fields_ = [("n_keep", C.c_int64), ("table_capacity", C.c_int64),
                 ("eps_screen", C.c_double), ("conv_tol", C.c_double),
                 ("n_lanczos", C.c_int32), ("max_iter", C.c_int32),
-                ("flags", C.c_uint32), ("reserved", C.c_int32)]
+                ("flags", C.c_uint32), ("bucket_elems", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -42,7 +42,8 @@ class StepInfo(C.Structure):
                 ("u_norm", C.c_double), ("t00", C.c_double),
                 ("n_in", C.c_int64), ("n_sigma", C.c_int64), ("n_kept", C.c_int64),
                 ("n_elements", C.c_int64), ("n_psi", C.c_int64),
-                ("ms_sigma", C.c_double), ("ms_step", C.c_double)]
+                ("ms_sigma", C.c_double), ("ms_step", C.c_double),
+                ("ms_emit", C.c_double), ("ms_merge", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -284,12 +285,12 @@ class Lanczos:
     """The SFCI solver (sfci_lanczos_create / _step / _vector / _destroy)."""
 
     def __init__(self, sys: System, init_rank, init_coef, n_keep, n_lanczos=10, max_iter=0,
-                 eps_screen=0.0, conv_tol=0.0, table_capacity=0, stream=None):
+                 eps_screen=0.0, conv_tol=0.0, table_capacity=0, bucket_elems=0, stream=None):
         self.sys = sys
         r = _dev(init_rank, torch.int64)
         c = _dev(init_coef, torch.float64)
         self.params = Params(int(n_keep), int(table_capacity), float(eps_screen), float(conv_tol),
-                             int(n_lanczos), int(max_iter), 0, 0)
+                             int(n_lanczos), int(max_iter), 0, int(bucket_elems))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         _check(lib().sfci_lanczos_create(C.byref(h), sys.handle, C.byref(self.params), _ptr(r),

@@ -36,7 +36,7 @@ __host__ __device__ inline size_t block_smem(const SysDev &d) {
 }
 
 __host__ __device__ inline size_t warp_smem(const SysDev &d) {
-    return align16(size_t(d.sa + d.sb) * 20 + 256);
+    return align16(size_t(d.sa + d.sb) * 12 + 192 * 8 + 256);
 }
 
 // single element h_ai + sum_{k occ alpha} (ai|kk) + sum_{k occ beta} (ai|kk)
@@ -91,12 +91,63 @@ __device__ double diagonal_element(const SysDev &d, const unsigned char *occA,
                      __dmul_rn(0.5, exch));
 }
 
-template <bool kDebug>
-__global__ void __launch_bounds__(kEmitThreads)
+// flip the sign of x when s is 1 (bit operation, exact; keeps the FP64 pipe free)
+__device__ __forceinline__ double flip(double x, unsigned s) {
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)s << 63));
+}
+
+__device__ __forceinline__ bool nonzero(double v) {
+    return ((unsigned long long)__double_as_longlong(v) << 1) != 0ull;
+}
+
+__device__ __forceinline__ void bucket_store(const BucketOut &B, unsigned b, unsigned pos,
+                                             unsigned long long tg, double v) {
+    const ulonglong2 sl = make_ulonglong2(tg, (unsigned long long)__double_as_longlong(v));
+    if (pos < B.cap) {
+        reinterpret_cast<ulonglong2 *>(B.elem)[size_t(b - B.lo) * B.cap + pos] = sl;
+    } else {
+        const unsigned long long q = atomicAdd(B.ovf_n, 1ull);
+        if ((long long)q < B.ovf_cap) reinterpret_cast<ulonglong2 *>(B.ovf)[q] = sl;
+        else atomicOr(B.status, 2);
+    }
+}
+
+constexpr int kU = 4;  // bucket reservations each lane keeps in flight
+
+// Is the element of target rank tg wanted by this launch?  (bucketed merge:
+// only buckets of the current pass)
+template <int kMode>
+__device__ __forceinline__ bool wanted(const EmitOut &o, unsigned long long tg) {
+    if (kMode != kModeBucket) return true;
+    const unsigned b = bucket_of(tg, o.b.log2B);
+    return b >= o.b.lo && b < o.b.hi;
+}
+
+// Deliver element e (unscaled) of source s with coefficient c to its target tg.
+template <int kMode>
+__device__ __forceinline__ void deliver(const EmitOut &o, long long di, long long s,
+                                        unsigned long long tg, double e, double c,
+                                        unsigned &inserted) {
+    if (kMode == kModeDebug) {
+        o.dsrc[di] = s;
+        o.dtgt[di] = tg;
+        o.delem[di] = e;
+        return;
+    }
+    const double v = __dmul_rn(e, c);
+    if (!nonzero(v)) return;
+    if (kMode == kModeTable) {
+        table_add(o.t, tg, v, inserted);
+        return;
+    }
+    const unsigned b = bucket_of(tg, o.b.log2B);
+    bucket_store(o.b, b, atomicAdd(&o.b.count[b], 1u), tg, v);
+}
+
+template <int kMode>
+__global__ void __launch_bounds__(kEmitThreads, 3)
 emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
-            const double *__restrict__ in_coef, long long n_in, Table t,
-            long long *__restrict__ dsrc, unsigned long long *__restrict__ dtgt,
-            double *__restrict__ delem) {
+            const double *__restrict__ in_coef, long long n_in, const EmitOut o) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int n = d.n, ks = d.ks;
     unsigned long long *bt = reinterpret_cast<unsigned long long *>(sm);
@@ -108,10 +159,9 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wb = sm + block_smem(d) + size_t(warp) * warp_smem(d);
     unsigned long long *rankA1 = reinterpret_cast<unsigned long long *>(wb);
-    double *elemA1 = reinterpret_cast<double *>(rankA1 + d.sa);
-    unsigned long long *rankB1 = reinterpret_cast<unsigned long long *>(elemA1 + d.sa);
-    double *elemB1 = reinterpret_cast<double *>(rankB1 + d.sb);
-    unsigned *offA1 = reinterpret_cast<unsigned *>(elemB1 + d.sb);
+    unsigned long long *rankB1 = rankA1 + d.sa;
+    unsigned long long *pre = rankB1 + d.sb;  // prefix sums A0 | A1 | A2, 64 each
+    unsigned *offA1 = reinterpret_cast<unsigned *>(pre + 192);
     unsigned *offB1 = offA1 + d.sa;
     unsigned char *occA = reinterpret_cast<unsigned char *>(offB1 + d.sb);
     unsigned char *virA = occA + 64, *occB = occA + 128, *virB = occA + 192;
@@ -128,7 +178,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
 
     for (long long s = gw; s < n_in; s += nw) {
         const unsigned long long r = in_rank[s];
-        const double c = kDebug ? 1.0 : in_coef[s];
+        const double c = kMode == kModeDebug ? 1.0 : in_coef[s];
         const unsigned long long hA = r / cb, hB = r - hA * cb;
         const unsigned long long alpha = string_unrank_warp(hA, n, d.na, bt, ks);
         const unsigned long long beta = string_unrank_warp(hB, n, d.nb, bt, ks);
@@ -136,86 +186,125 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
 
         build_lists(alpha, beta, n, occA, virA, occB, virB);
         __syncwarp();
-        // single-excitation tables
+        // single-excitation tables: Eq. 12 index of the excited string, g row
+        // offset, hop sign (bit 31)
         for (int x = lane; x < d.sa; x += 32) {
             const int io = x / d.va, iv = x - io * d.va;
             const int i = occA[io], a = virA[iv];
-            const int sg = parity64(alpha & between_mask(i, a));
+            const unsigned sg = parity64(alpha & between_mask(i, a));
             rankA1[x] = string_rank(alpha ^ (1ull << i) ^ (1ull << a), bt, ks);
-            const double F = single_element(d, i, a, occA, occB, occA, d.na);
-            elemA1[x] = sg ? -F : F;
-            offA1[x] = unsigned((a * n + i) * n2) | (unsigned(sg) << 31);
+            offA1[x] = unsigned((a * n + i) * n2) | (sg << 31);
         }
         for (int y = lane; y < d.sb; y += 32) {
             const int jo = y / d.vb, jv = y - jo * d.vb;
             const int j = occB[jo], b = virB[jv];
-            const int sg = parity64(beta & between_mask(j, b));
+            const unsigned sg = parity64(beta & between_mask(j, b));
             rankB1[y] = string_rank(beta ^ (1ull << j) ^ (1ull << b), bt, ks);
-            const double F = single_element(d, j, b, occA, occB, occB, d.nb);
-            elemB1[y] = sg ? -F : F;
-            offB1[y] = unsigned(b * n + j) | (unsigned(sg) << 31);
+            offB1[y] = unsigned(b * n + j) | (sg << 31);
         }
         __syncwarp();
 
         // diagonal
-        if (lane == 0) {
-            const double e = diagonal_element(d, occA, occB);
-            if (kDebug) {
-                dsrc[base] = s, dtgt[base] = r, delem[base] = e;
-            } else {
-                const double v = __dmul_rn(e, c);
-                if (v != 0.0) table_add(t, r, v, inserted);
-            }
-        }
-        // singles
+        if (lane == 0 && wanted<kMode>(o, r))
+            deliver<kMode>(o, base, s, r, diagonal_element(d, occA, occB), c, inserted);
+        // singles; the element is only evaluated for wanted targets
         long long off = base + 1;
         for (int x = lane; x < d.sa; x += 32) {
             const unsigned long long tg = rankA1[x] * cb + hB;
-            if (kDebug) {
-                dsrc[off + x] = s, dtgt[off + x] = tg, delem[off + x] = elemA1[x];
-            } else {
-                const double v = __dmul_rn(elemA1[x], c);
-                if (v != 0.0) table_add(t, tg, v, inserted);
-            }
+            if (!wanted<kMode>(o, tg)) continue;
+            const int io = x / d.va, iv = x - io * d.va;
+            const double F = single_element(d, occA[io], virA[iv], occA, occB, occA, d.na);
+            deliver<kMode>(o, off + x, s, tg, flip(F, offA1[x] >> 31), c, inserted);
         }
         off += d.sa;
         for (int y = lane; y < d.sb; y += 32) {
             const unsigned long long tg = hA * cb + rankB1[y];
-            if (kDebug) {
-                dsrc[off + y] = s, dtgt[off + y] = tg, delem[off + y] = elemB1[y];
-            } else {
-                const double v = __dmul_rn(elemB1[y], c);
-                if (v != 0.0) table_add(t, tg, v, inserted);
-            }
+            if (!wanted<kMode>(o, tg)) continue;
+            const int jo = y / d.vb, jv = y - jo * d.vb;
+            const double F = single_element(d, occB[jo], virB[jv], occA, occB, occB, d.nb);
+            deliver<kMode>(o, off + y, s, tg, flip(F, offB1[y] >> 31), c, inserted);
         }
         off += d.sb;
-        // same-spin doubles: (i<j) -> (a<b), i->a then j->b
+        // same-spin doubles (i<j) -> (a<b), i->a then j->b.  The index of the
+        // excited string comes from prefix sums over the M-2 spectators r_t:
+        //   A0[m] = sum_{t<=m} C(r_t, t), A1[m] = sum C(r_t, t+1), A2[m] = sum C(r_t, t+2);
+        //   h = A0[q1] + C(a, q1+1) + A1[q2] - A1[q1] + C(b, q2+2) + A2[M-2] - A2[q2]
+        // with q1, q2 the spectators below a and below b (Eq. 12 term by term).
         for (int spin = 0; spin < 2; ++spin) {
             const unsigned long long str = spin ? beta : alpha;
             const unsigned char *occ = spin ? occB : occA, *vir = spin ? virB : virA;
             const unsigned char *po = spin ? pOB : pOA, *pv = spin ? pVB : pVA;
             const int npo = spin ? d.po_b : d.po_a, npv = spin ? d.pv_b : d.pv_a;
+            const int M = spin ? d.nb : d.na;
             for (int p = 0; p < npo; ++p) {
-                const int i = occ[po[2 * p]], j = occ[po[2 * p + 1]];
-                for (int q = lane; q < npv; q += 32) {
-                    const int a = vir[pv[2 * q]], b = vir[pv[2 * q + 1]];
-                    const int s1 = parity64(str & between_mask(i, a));
-                    const unsigned long long s1s = str ^ (1ull << i) ^ (1ull << a);
-                    const int s2 = parity64(s1s & between_mask(j, b));
-                    const unsigned long long s2s = s1s ^ (1ull << j) ^ (1ull << b);
-                    double e = __dsub_rn(__ldg(&g[(size_t(a * n + i) * n + b) * n + j]),
-                                         __ldg(&g[(size_t(a * n + j) * n + b) * n + i]));
-                    if (s1 ^ s2) e = -e;
-                    const unsigned long long h2 = string_rank(s2s, bt, ks);
-                    const unsigned long long tg = spin ? hA * cb + h2 : h2 * cb + hB;
-                    if (kDebug) {
-                        const long long o = off + (long long)p * npv + q;
-                        dsrc[o] = s, dtgt[o] = tg, delem[o] = e;
-                    } else {
-                        const double v = __dmul_rn(e, c);
-                        if (v != 0.0) table_add(t, tg, v, inserted);
+                const int io = po[2 * p], jo = po[2 * p + 1];
+                const int i = occ[io], j = occ[jo];
+                const unsigned long long rem = str ^ (1ull << i) ^ (1ull << j);
+                {
+                    unsigned long long c0 = 0, c1 = 0, c2 = 0;
+                    if (lane < M - 2) {
+                        int t = lane;
+                        if (t >= io) ++t;
+                        if (t >= jo) ++t;
+                        const int e = occ[t];
+                        c0 = bt[e * ks + lane + 1];
+                        c1 = bt[e * ks + lane + 2];
+                        c2 = bt[e * ks + lane + 3];
+                    }
+                    for (int w = 1; w < 32; w <<= 1) {
+                        const unsigned long long y0 = __shfl_up_sync(kFull, c0, w);
+                        const unsigned long long y1 = __shfl_up_sync(kFull, c1, w);
+                        const unsigned long long y2 = __shfl_up_sync(kFull, c2, w);
+                        if (lane >= w) c0 += y0, c1 += y1, c2 += y2;
+                    }
+                    if (lane < M - 2) pre[lane + 1] = c0, pre[64 + lane + 1] = c1, pre[128 + lane + 1] = c2;
+                    if (lane == 0) pre[0] = 0, pre[64] = 0, pre[128] = 0;
+                }
+                __syncwarp();
+                const unsigned long long a2top = pre[128 + (M - 2)];
+                for (int q0 = lane; q0 < npv; q0 += 32 * kU) {
+                    unsigned long long tgk[kU];
+                    double vk[kU];
+                    unsigned bk[kU], pk[kU];
+                    bool ok[kU];
+#pragma unroll
+                    for (int k = 0; k < kU; ++k) {
+                        const int q = q0 + 32 * k;
+                        ok[k] = false;
+                        if (q >= npv) continue;
+                        const int a = vir[pv[2 * q]], b = vir[pv[2 * q + 1]];
+                        const int q1 = __popcll(rem & ((1ull << a) - 1ull));
+                        const int q2 = __popcll(rem & ((1ull << b) - 1ull));
+                        const unsigned long long h2 = pre[q1] + bt[a * ks + q1 + 1] + pre[64 + q2] -
+                                                      pre[64 + q1] + bt[b * ks + q2 + 2] + a2top -
+                                                      pre[128 + q2];
+                        const unsigned long long tg = spin ? hA * cb + h2 : h2 * cb + hB;
+                        if (!wanted<kMode>(o, tg)) continue;
+                        const int s1 = parity64(str & between_mask(i, a));
+                        const unsigned long long s1s = str ^ (1ull << i) ^ (1ull << a);
+                        const int s2 = parity64(s1s & between_mask(j, b));
+                        const double e = flip(__dsub_rn(__ldg(&g[(size_t(a * n + i) * n + b) * n + j]),
+                                                        __ldg(&g[(size_t(a * n + j) * n + b) * n + i])),
+                                              unsigned(s1 ^ s2));
+                        if (kMode != kModeBucket) {
+                            deliver<kMode>(o, off + (long long)p * npv + q, s, tg, e, c, inserted);
+                            continue;
+                        }
+                        vk[k] = __dmul_rn(e, c);
+                        tgk[k] = tg;
+                        bk[k] = bucket_of(tg, o.b.log2B);
+                        ok[k] = nonzero(vk[k]);
+                    }
+                    if (kMode == kModeBucket) {
+#pragma unroll
+                        for (int k = 0; k < kU; ++k)
+                            if (ok[k]) pk[k] = atomicAdd(&o.b.count[bk[k]], 1u);
+#pragma unroll
+                        for (int k = 0; k < kU; ++k)
+                            if (ok[k]) bucket_store(o.b, bk[k], pk[k], tgk[k], vk[k]);
                     }
                 }
+                __syncwarp();
             }
             off += (long long)npo * npv;
         }
@@ -225,25 +314,44 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             const unsigned oa = offA1[x];
             const double *gx = g + (oa & 0x7fffffffu);
             const unsigned sa = oa >> 31;
-            for (int y = lane; y < d.sb; y += 32) {
-                const unsigned ob = offB1[y];
-                double e = __ldg(&gx[ob & 0x7fffffffu]);
-                if (sa ^ (ob >> 31)) e = -e;
-                const unsigned long long tg = ra + rankB1[y];
-                if (kDebug) {
-                    const long long o = off + (long long)x * d.sb + y;
-                    dsrc[o] = s, dtgt[o] = tg, delem[o] = e;
-                } else {
-                    const double v = __dmul_rn(e, c);
-                    if (v != 0.0) table_add(t, tg, v, inserted);
+            for (int y0 = lane; y0 < d.sb; y0 += 32 * kU) {
+                unsigned long long tgk[kU];
+                double vk[kU];
+                unsigned bk[kU], pk[kU];
+                bool ok[kU];
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int y = y0 + 32 * k;
+                    ok[k] = false;
+                    if (y >= d.sb) continue;
+                    const unsigned long long tg = ra + rankB1[y];
+                    if (!wanted<kMode>(o, tg)) continue;
+                    const unsigned ob = offB1[y];
+                    const double e = flip(__ldg(&gx[ob & 0x7fffffffu]), sa ^ (ob >> 31));
+                    if (kMode != kModeBucket) {
+                        deliver<kMode>(o, off + (long long)x * d.sb + y, s, tg, e, c, inserted);
+                        continue;
+                    }
+                    vk[k] = __dmul_rn(e, c);
+                    tgk[k] = tg;
+                    bk[k] = bucket_of(tg, o.b.log2B);
+                    ok[k] = nonzero(vk[k]);
+                }
+                if (kMode == kModeBucket) {
+#pragma unroll
+                    for (int k = 0; k < kU; ++k)
+                        if (ok[k]) pk[k] = atomicAdd(&o.b.count[bk[k]], 1u);
+#pragma unroll
+                    for (int k = 0; k < kU; ++k)
+                        if (ok[k]) bucket_store(o.b, bk[k], pk[k], tgk[k], vk[k]);
                 }
             }
         }
         __syncwarp();
     }
-    if (!kDebug) {
-        for (int o = 16; o > 0; o >>= 1) inserted += __shfl_xor_sync(kFull, inserted, o);
-        if (lane == 0 && inserted) atomicAdd(t.count, (unsigned long long)inserted);
+    if (kMode == kModeTable) {
+        for (int w = 16; w > 0; w >>= 1) inserted += __shfl_xor_sync(kFull, inserted, w);
+        if (lane == 0 && inserted) atomicAdd(o.t.count, (unsigned long long)inserted);
     }
 }
 
@@ -305,13 +413,13 @@ int device_sms() {
     return sms > 0 ? sms : 1;
 }
 
-template <bool kDebug>
+template <int kMode>
 cudaError_t launch_emit_impl(const SysDev &d, const unsigned long long *in_rank,
-                             const double *in_coef, long long n_in, Table t, long long *src,
-                             unsigned long long *tgt, double *elem, cudaStream_t st) {
+                             const double *in_coef, long long n_in, const EmitOut &o,
+                             cudaStream_t st) {
     if (n_in <= 0) return cudaSuccess;
     const size_t smem = emit_smem_bytes(d, kEmitWarps);
-    auto kern = emit_kernel<kDebug>;
+    auto kern = emit_kernel<kMode>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -322,7 +430,7 @@ cudaError_t launch_emit_impl(const SysDev &d, const unsigned long long *in_rank,
     long long grid = (long long)device_sms() * per_sm;
     if (want < grid) grid = want;
     count_launch();
-    kern<<<(unsigned)grid, kEmitThreads, smem, st>>>(d, in_rank, in_coef, n_in, t, src, tgt, elem);
+    kern<<<(unsigned)grid, kEmitThreads, smem, st>>>(d, in_rank, in_coef, n_in, o);
     return cudaGetLastError();
 }
 
@@ -334,14 +442,25 @@ size_t emit_smem_bytes(const SysDev &d, int warps) {
 
 cudaError_t launch_emit(const SysDev &d, const unsigned long long *in_rank, const double *in_coef,
                         long long n_in, Table t, cudaStream_t st) {
-    return launch_emit_impl<false>(d, in_rank, in_coef, n_in, t, nullptr, nullptr, nullptr, st);
+    EmitOut o{};
+    o.t = t;
+    return launch_emit_impl<kModeTable>(d, in_rank, in_coef, n_in, o, st);
+}
+
+cudaError_t launch_emit_buckets(const SysDev &d, const unsigned long long *in_rank,
+                                const double *in_coef, long long n_in, const BucketOut &b,
+                                cudaStream_t st) {
+    EmitOut o{};
+    o.b = b;
+    return launch_emit_impl<kModeBucket>(d, in_rank, in_coef, n_in, o, st);
 }
 
 cudaError_t launch_debug_excitations(const SysDev &d, const unsigned long long *in_rank,
                                      long long n_in, long long *src, unsigned long long *tgt,
                                      double *elem, cudaStream_t st) {
-    Table t{};
-    return launch_emit_impl<true>(d, in_rank, nullptr, n_in, t, src, tgt, elem, st);
+    EmitOut o{};
+    o.dsrc = src, o.dtgt = tgt, o.delem = elem;
+    return launch_emit_impl<kModeDebug>(d, in_rank, nullptr, n_in, o, st);
 }
 
 cudaError_t launch_rank(const SysDev &d, const unsigned long long *a, const unsigned long long *b,

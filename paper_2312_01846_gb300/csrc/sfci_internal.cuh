@@ -274,6 +274,59 @@ cudaError_t table_dots(Table t, const VecRef *vecs_host, int nvec, double *out_d
 cudaError_t vec_overlaps(const VecRef *vecs_host, int nvec, VecRef last, double *out_dev,
                          void *ws, cudaStream_t st);
 
+// sfci_merge.cu -- bucketed merge (see the file's header)
+struct Probe {
+    unsigned long long key;    // rank of a basis-vector entry
+    unsigned long long where;  // vector index j << 40 | position in w_j
+};
+struct VecPackRef {
+    VecRef v[kMaxVec];
+};
+struct SigPack {
+    double *p[kMaxVec];
+};
+struct MergeArgs {
+    unsigned lo, hi, cap;
+    int log2B;
+    const unsigned *count;              // [B] elements per bucket
+    const Slot *elem;                   // pass buckets' regions, cap each
+    const Slot *ovf_sorted;             // overflow elements sorted by bucket
+    const unsigned long long *ovf_off;  // [hi - lo + 1]
+    long long ovf_cap;                  // entries of ovf_sorted
+    const Probe *probes;                // sorted by bucket
+    const unsigned long long *probe_off;  // [B + 1]
+    double *sigw[kMaxVec];              // sigma recorded at w_j's entries
+    int ja, jb;                         // vectors whose entries stay out of the stream (w_i, w_{i-1}); -1 none
+    double eps;                         // screen
+    unsigned long long *out_key;
+    double *out_val;
+    long long out_cap;
+    unsigned long long *out_n;
+    unsigned long long *hist;           // [4096] top-12-bit histogram of |streamed values|
+    double *sumsq;
+    unsigned long long *n_live;         // entries that survive the screen
+    unsigned *queue;
+    int *status;                        // bit 2: a bucket has too many distinct keys; bit 3: output full
+};
+size_t scan_ws_bytes(long long m);
+cudaError_t exclusive_scan(const unsigned *in, long long m, unsigned long long *out, void *ws,
+                           cudaStream_t st);
+cudaError_t sort_overflow(const unsigned *count, unsigned lo, unsigned nb, unsigned cap,
+                          const Slot *ovf, const unsigned long long *ovf_n, long long ovf_cap,
+                          int log2B, unsigned *tmp_counts, unsigned long long *off, void *scan_ws,
+                          Slot *out, cudaStream_t st);
+cudaError_t sort_probes(const VecRef *vecs, int nvec, int log2B, unsigned *pcount,
+                        unsigned long long *poff, void *scan_ws, Probe *out, cudaStream_t st);
+// slots: shared-memory table size (2048, 4096 or 8192 keys)
+cudaError_t launch_merge(const MergeArgs &A, int slots, cudaStream_t st);
+cudaError_t launch_u_entries(VecRef wi, const double *sig_i, VecRef wm, const double *sig_m,
+                             double a, double b, unsigned long long *out_key, double *out_val,
+                             unsigned long long base_n, long long out_cap, unsigned long long *hist,
+                             double *sumsq, int *status, cudaStream_t st);
+size_t aligned_dots_ws_bytes(int nvec);
+cudaError_t aligned_dots(const VecRef *vecs, double *const *sig, int nvec, double *out_dev, void *ws,
+                         cudaStream_t st);
+
 // sfci_select.cu
 size_t select_workspace_bytes(long long n_items, long long k);
 // Generic source of (key, val) items: either SoA arrays (stride 1) or table
@@ -290,6 +343,20 @@ struct Items {
 cudaError_t select_topk(Items it, long long k, unsigned long long *out_key, double *out_val,
                         unsigned long long *n_out_dev, double *sumsq_dev,
                         unsigned long long *total_dev, void *ws, size_t ws_bytes, cudaStream_t st);
+// Two-level top-k over items whose first-digit histogram (top 12 bits of the
+// composite key, 4096 bins) is already known: pick the bin, then one pass
+// writes every item of a smaller bin to out and every item of the picked bin
+// to cand.  *state_host receives {n_out, n_cand, need, all, done}; the caller
+// finishes with select_topk over the candidates when !done.
+struct SplitResult {
+    unsigned long long n_out, n_cand, need, total;
+    int all, done;
+};
+cudaError_t select_split(Items it, long long k, const unsigned long long *hist0,
+                         unsigned long long *out_key, double *out_val, unsigned long long *n_out_dev,
+                         unsigned long long *cand_key, double *cand_val, long long cand_cap,
+                         unsigned long long *cand_n, void *ws, size_t ws_bytes, SplitResult *res_host,
+                         cudaStream_t st);
 size_t sort_workspace_bytes(long long n);
 // stable LSD radix sort of (key, val) by key on the low `bits` bits; result in
 // key/val (uses ws as ping-pong buffers); n read from the device when n_dev

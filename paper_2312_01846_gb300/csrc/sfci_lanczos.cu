@@ -167,6 +167,24 @@ struct sfci_lanczos {
     double e_prev = 0.0;
     long long m_prev = 0, nin_prev = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t evp[4] = {nullptr, nullptr, nullptr, nullptr};  // emit / merge timing
+    // bucketed sigma (sfci_merge.cu); every buffer with its allocated bytes
+    struct Buf {
+        void *p = nullptr;
+        size_t bytes = 0;
+    };
+    Buf bcount, belem, bovf, bovf_sorted, tmp_counts, ovf_off, probes, pcount, poff, scan_ws,
+        sig_key, sig_val, cand_key, cand_val;
+    long long sig_cap = 0, ovf_cap = 0, cand_cap = 0;
+    double *sigw[kMaxVec] = {};
+    char *words = nullptr;  // hist[4096] | outn | mlive | ovf_n | cand_n | msumsq | queue | mstatus
+    unsigned long long *hist = nullptr, *outn = nullptr, *mlive = nullptr, *ovf_n = nullptr,
+                       *cand_n = nullptr;
+    double *msumsq = nullptr;
+    unsigned *queue = nullptr;
+    int *mstatus = nullptr;
+    int log2B_last = 0;
+    double ms_emit = 0, ms_merge = 0;
 };
 
 namespace {
@@ -177,7 +195,15 @@ void destroy_lz(sfci_lanczos *z) {
     for (auto p : z->wc) cudaFree(p);
     cudaFree(z->slots);
     cudaFree(z->scratch);
+    for (auto *b : {&z->bcount, &z->belem, &z->bovf, &z->bovf_sorted, &z->tmp_counts, &z->ovf_off,
+                    &z->probes, &z->pcount, &z->poff, &z->scan_ws, &z->sig_key, &z->sig_val,
+                    &z->cand_key, &z->cand_val})
+        cudaFree(b->p);
+    cudaFree(z->words);
+    for (int j = 0; j < kMaxVec; ++j) cudaFree(z->sigw[j]);
     for (auto &e : z->ev)
+        if (e) cudaEventDestroy(e);
+    for (auto &e : z->evp)
         if (e) cudaEventDestroy(e);
     delete z;
 }
@@ -227,6 +253,176 @@ sfci_status table_topk(sfci_lanczos *z, unsigned long long cap, int dst, double 
     SFCI_CUDA(cudaStreamSynchronize(z->st));
     z->wn[dst] = (long long)std::min<unsigned long long>(hn, (unsigned long long)z->nkeep);
     return SFCI_OK;
+}
+
+// make buffer b hold at least `want` bytes (contents are not kept)
+sfci_status ensure(sfci_lanczos::Buf &b, size_t want, cudaStream_t st, const char *what) {
+    if (b.p && b.bytes >= want) return SFCI_OK;
+    SFCI_CUDA(cudaStreamSynchronize(st));
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, want > 0 ? want : 16);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
+        return SFCI_E_NOMEM;
+    }
+    b.bytes = want;
+    return SFCI_OK;
+}
+
+template <class T>
+T *P(const sfci_lanczos::Buf &b) {
+    return static_cast<T *>(b.p);
+}
+
+// sigma_i = H w_i through the bucketed merge, with the probes of w_0..w_i.
+// On return the streamed entries sit in sig_key/sig_val[0, *n_out) and sigma at
+// every basis entry in sigw[j].
+sfci_status bucketed_sigma(sfci_lanczos *z, int i, unsigned long long *n_out, unsigned long long *n_live,
+                           double *sumsq) {
+    const SysDev &d = z->sys->d;
+    const long long n_in = z->wn[i];
+    const double E = (double)n_in * (double)(d.n_conn + 1);
+    // buckets of ~bucket_elems elements; the merge table holds twice that many keys
+    const double per_bucket = z->p.bucket_elems > 0 ? (double)z->p.bucket_elems : 2048.0;
+    const int slots = per_bucket <= 1024.0 ? 2048 : (per_bucket <= 2048.0 ? 4096 : 8192);
+    int log2B = 4;
+    while (log2B < 28 && (double)(1ull << log2B) * per_bucket < E) ++log2B;
+    if (z->log2B_last > log2B) log2B = z->log2B_last;  // raised after a too-full bucket
+    // streamed-output capacity from the previous step (or the element count)
+    double sig_need;
+    if (z->m_prev > 0 && z->nin_prev > 0)
+        sig_need = 1.3 * (double)z->m_prev * std::max(1.0, (double)n_in / (double)z->nin_prev);
+    else
+        sig_need = E;
+    sig_need = std::min(sig_need, E) + 2.0 * (double)z->nkeep + 1024.0;
+    long long ovf_cap = std::max<long long>(1 << 20, z->ovf_cap);
+    long long totp = 0;
+    for (int j = 0; j <= i; ++j) totp += z->wn[j];
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        const unsigned long long B = 1ull << log2B;
+        size_t free_b = 0, tot_b = 0;
+        SFCI_CUDA(cudaMemGetInfo(&free_b, &tot_b));
+        // memory the element regions may use: what is free plus what the big buffers hold
+        const double held = (double)z->belem.bytes + (double)z->sig_key.bytes + (double)z->sig_val.bytes;
+        const double budget = 0.85 * ((double)free_b + held) - sig_need * 16.0 - 2.0 * ovf_cap * 16.0;
+        const unsigned cap = (unsigned)(std::ceil(1.125 * E / (double)B) + 128.0) & ~7u;
+        if (budget <= (double)cap * sizeof(Slot)) {
+            set_error("not enough device memory for sigma");
+            return SFCI_E_CAPACITY;
+        }
+        int npass = 1;
+        while ((double)((B + npass - 1) / npass) * cap * sizeof(Slot) > budget && npass < 4096) ++npass;
+        const unsigned long long Bp = (B + npass - 1) / npass;
+        const long long scap = (long long)sig_need;
+        sfci_status r;
+        const size_t want_elem = size_t(Bp) * cap * sizeof(Slot), want_sig = size_t(scap) * 8;
+        if (z->belem.bytes < want_elem || z->sig_key.bytes < want_sig || z->sig_val.bytes < want_sig) {
+            // the three large buffers are sized together from one budget: free them all first
+            SFCI_CUDA(cudaStreamSynchronize(z->st));
+            for (auto *bb : {&z->belem, &z->sig_key, &z->sig_val}) {
+                cudaFree(bb->p);
+                bb->p = nullptr;
+                bb->bytes = 0;
+            }
+        }
+        if ((r = ensure(z->sig_key, want_sig, z->st, "sigma keys"))) return r;
+        if ((r = ensure(z->sig_val, want_sig, z->st, "sigma values"))) return r;
+        z->sig_cap = scap;
+        if ((r = ensure(z->belem, want_elem, z->st, "element regions"))) return r;
+        if ((r = ensure(z->bcount, size_t(B) * 4, z->st, "bucket counters"))) return r;
+        if ((r = ensure(z->probes, size_t(std::max<long long>(totp, 1)) * sizeof(Probe), z->st, "probes"))) return r;
+        if ((r = ensure(z->pcount, size_t(B) * 4, z->st, "probe counts"))) return r;
+        if ((r = ensure(z->poff, size_t(B + 1) * 8, z->st, "probe offsets"))) return r;
+        if ((r = ensure(z->tmp_counts, size_t(B + 1) * 4, z->st, "overflow counts"))) return r;
+        if ((r = ensure(z->ovf_off, size_t(B + 1) * 8, z->st, "overflow offsets"))) return r;
+        if ((r = ensure(z->bovf, size_t(ovf_cap) * sizeof(Slot), z->st, "overflow list"))) return r;
+        if ((r = ensure(z->bovf_sorted, size_t(ovf_cap) * sizeof(Slot), z->st, "sorted overflow"))) return r;
+        z->ovf_cap = ovf_cap;
+        if ((r = ensure(z->scan_ws, scan_ws_bytes((long long)B + 1), z->st, "scan workspace"))) return r;
+        for (int j = 0; j <= i; ++j)
+            if (!z->sigw[j]) SFCI_CUDA(cudaMalloc(&z->sigw[j], size_t(z->nkeep) * 8));
+
+        // probes of w_0..w_i, bucketed once for all passes
+        std::vector<VecRef> vr(i + 1);
+        for (int j = 0; j <= i; ++j) vr[j] = VecRef{z->wr[j], z->wc[j], z->wn[j]};
+        SFCI_CUDA(sort_probes(vr.data(), i + 1, log2B, P<unsigned>(z->pcount), P<unsigned long long>(z->poff),
+                              z->scan_ws.p, P<Probe>(z->probes), z->st));
+        SFCI_CUDA(cudaMemsetAsync(z->bcount.p, 0, B * 4, z->st));
+        SFCI_CUDA(cudaMemsetAsync(z->words, 0, 4096 * 8 + 1024, z->st));
+        z->ms_emit = z->ms_merge = 0.0;
+        for (int pass = 0; pass < npass; ++pass) {
+            const unsigned lo = (unsigned)(pass * Bp);
+            const unsigned hi = (unsigned)std::min<unsigned long long>(B, (pass + 1) * Bp);
+            if (lo >= hi) break;
+            SFCI_CUDA(cudaMemsetAsync(z->ovf_n, 0, 8, z->st));
+            BucketOut bo;
+            bo.count = P<unsigned>(z->bcount);
+            bo.elem = P<Slot>(z->belem);
+            bo.ovf = P<Slot>(z->bovf);
+            bo.ovf_n = z->ovf_n;
+            bo.ovf_cap = z->ovf_cap;
+            bo.log2B = log2B;
+            bo.lo = lo, bo.hi = hi, bo.cap = cap;
+            bo.status = z->mstatus;
+            SFCI_CUDA(cudaEventRecord(z->evp[0], z->st));
+            SFCI_CUDA(launch_emit_buckets(d, z->wr[i], z->wc[i], n_in, bo, z->st));
+            SFCI_CUDA(cudaEventRecord(z->evp[1], z->st));
+            SFCI_CUDA(sort_overflow(P<unsigned>(z->bcount), lo, hi - lo, cap, P<Slot>(z->bovf), z->ovf_n,
+                                    z->ovf_cap, log2B, P<unsigned>(z->tmp_counts),
+                                    P<unsigned long long>(z->ovf_off), z->scan_ws.p, P<Slot>(z->bovf_sorted),
+                                    z->st));
+            MergeArgs A{};
+            A.lo = lo, A.hi = hi, A.cap = cap, A.log2B = log2B;
+            A.count = P<unsigned>(z->bcount);
+            A.elem = P<Slot>(z->belem);
+            A.ovf_sorted = P<Slot>(z->bovf_sorted);
+            A.ovf_off = P<unsigned long long>(z->ovf_off);
+            A.ovf_cap = z->ovf_cap;
+            A.probes = P<Probe>(z->probes);
+            A.probe_off = P<unsigned long long>(z->poff);
+            for (int j = 0; j <= i; ++j) A.sigw[j] = z->sigw[j];
+            A.ja = i;
+            A.jb = i > 0 ? i - 1 : -1;
+            A.eps = z->p.eps_screen > 0.0 ? z->p.eps_screen : 0.0;
+            A.out_key = P<unsigned long long>(z->sig_key);
+            A.out_val = P<double>(z->sig_val);
+            A.out_cap = z->sig_cap;
+            A.out_n = z->outn;
+            A.hist = z->hist;
+            A.sumsq = z->msumsq;
+            A.n_live = z->mlive;
+            A.queue = z->queue;
+            A.status = z->mstatus;
+            SFCI_CUDA(launch_merge(A, slots, z->st));
+            SFCI_CUDA(cudaEventRecord(z->evp[2], z->st));
+            SFCI_CUDA(cudaEventSynchronize(z->evp[2]));
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, z->evp[0], z->evp[1]);
+            cudaEventElapsedTime(&b, z->evp[1], z->evp[2]);
+            z->ms_emit += a, z->ms_merge += b;
+        }
+        int hs = 0;
+        unsigned long long ho = 0, hl = 0, hv = 0;
+        double hq = 0.0;
+        SFCI_CUDA(cudaMemcpyAsync(&hs, z->mstatus, 4, cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(&ho, z->outn, 8, cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(&hl, z->mlive, 8, cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(&hv, z->ovf_n, 8, cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(&hq, z->msumsq, 8, cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaStreamSynchronize(z->st));
+        if (hs == 0) {
+            z->log2B_last = 0;
+            *n_out = ho, *n_live = hl, *sumsq = hq;
+            return SFCI_OK;
+        }
+        if (hs & 2) ovf_cap *= 4;
+        if (hs & 4) log2B += 1, z->log2B_last = log2B;
+        if (hs & 8) sig_need = std::max(sig_need * 2.0, (double)ho * 1.3 + 2.0 * z->nkeep);
+    }
+    set_error("bucketed sigma did not fit after 8 attempts");
+    return SFCI_E_CAPACITY;
 }
 
 // w_0 = normalise(top_{N_d}(trial vector)); a new cycle begins
@@ -304,6 +500,19 @@ sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
     z->off_small = o, o = a256(o + 4096 + sizeof(double) * 2 * kMaxVec);
     if (e == cudaSuccess) e = cudaMalloc(&z->scratch, o);
     for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&z->ev[k]);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&z->evp[k]);
+    if (e == cudaSuccess) e = cudaMalloc(&z->words, 4096 * 8 + 1024);
+    if (e == cudaSuccess) {
+        z->hist = reinterpret_cast<unsigned long long *>(z->words);
+        char *w = z->words + 4096 * 8;
+        z->outn = reinterpret_cast<unsigned long long *>(w);
+        z->mlive = reinterpret_cast<unsigned long long *>(w + 8);
+        z->ovf_n = reinterpret_cast<unsigned long long *>(w + 16);
+        z->cand_n = reinterpret_cast<unsigned long long *>(w + 24);
+        z->msumsq = reinterpret_cast<double *>(w + 32);
+        z->queue = reinterpret_cast<unsigned *>(w + 40);
+        z->mstatus = reinterpret_cast<int *>(w + 44);
+    }
     if (e != cudaSuccess) {
         destroy_lz(z);
         set_error(std::string("sfci_lanczos_create: ") + cudaGetErrorString(e));
@@ -345,56 +554,28 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
     const long long n_in = z->wn[i];
     SFCI_CUDA(cudaEventRecord(z->ev[0], z->st));
 
-    // ---- sigma_i = H w_i into the table, grown and redone if it overflows
-    double est;
-    if (z->m_prev > 0 && z->nin_prev > 0)
-        est = 1.25 * (double)z->m_prev * std::max(1.0, (double)n_in / (double)z->nin_prev);
-    else
-        est = (double)n_in * (double)(d.n_conn + 1);
-    est += 2.0 * (double)z->nkeep;
-    double want = std::max(65536.0, 2.0 * est);
-    unsigned long long cap = want >= (double)z->budget ? z->budget : next_pow2((unsigned long long)want);
-    unsigned long long hcount = 0;
-    for (;;) {
-        sfci_status rs = ensure_slots(z, cap);
+    // ---- sigma_i = H w_i, bucketed merge with the probes of w_0..w_i
+    unsigned long long n_stream = 0, n_live = 0;
+    double sq = 0.0;
+    {
+        const sfci_status rs = bucketed_sigma(z, i, &n_stream, &n_live, &sq);
         if (rs != SFCI_OK) return rs;
-        Table t = make_table(z, cap);
-        SFCI_CUDA(table_clear(t, z->st));
-        SFCI_CUDA(cudaEventRecord(z->ev[1], z->st));
-        SFCI_CUDA(launch_emit(d, z->wr[i], z->wc[i], n_in, t, z->st));
-        SFCI_CUDA(cudaEventRecord(z->ev[2], z->st));
-        int hstatus = 0;
-        SFCI_CUDA(cudaMemcpyAsync(&hstatus, z->tstatus, sizeof(int), cudaMemcpyDeviceToHost, z->st));
-        SFCI_CUDA(cudaMemcpyAsync(&hcount, z->tcount, 8, cudaMemcpyDeviceToHost, z->st));
-        SFCI_CUDA(cudaStreamSynchronize(z->st));
-        const bool full = (hstatus & 1) ||
-                          (double)hcount + 2.0 * (double)z->nkeep > 0.85 * (double)cap;
-        if (!full) break;
-        if (cap >= z->budget) {
-            set_error("sigma's merge table needs more device memory than is free");
-            return SFCI_E_CAPACITY;
-        }
-        cap = std::min(cap * 4, z->budget);
     }
-    float ms_sigma = 0.f;
-    cudaEventElapsedTime(&ms_sigma, z->ev[1], z->ev[2]);
-    info->ms_sigma = ms_sigma;
+    info->ms_sigma = z->ms_emit + z->ms_merge;
+    info->ms_emit = z->ms_emit;
+    info->ms_merge = z->ms_merge;
     info->n_elements = n_in * (d.n_conn + 1);
-    z->m_prev = (long long)hcount;
+    z->m_prev = (long long)n_stream;
     z->nin_prev = n_in;
-    Table t = make_table(z, cap);
-    SFCI_CUDA(table_screen(t, z->p.eps_screen, z->screened, z->st));
 
-    // ---- T_ji = <w_j|sigma_i>, S_ji = <w_j|w_i>, j <= i
+    // ---- T_ji = <w_j|sigma_i> from sigma recorded at w_j's entries, S_ji = <w_j|w_i>
     std::vector<VecRef> vr(i + 1);
     for (int j = 0; j <= i; ++j) vr[j] = VecRef{z->wr[j], z->wc[j], z->wn[j]};
-    SFCI_CUDA(table_dots(t, vr.data(), i + 1, z->dT, z->scratch + z->off_dots, z->st));
+    SFCI_CUDA(aligned_dots(vr.data(), z->sigw, i + 1, z->dT, z->scratch + z->off_dots, z->st));
     SFCI_CUDA(vec_overlaps(vr.data(), i + 1, vr[i], z->dS, z->scratch + z->off_dots, z->st));
     std::vector<double> tcol(i + 1), scol(i + 1);
-    unsigned long long hscreened = 0;
     SFCI_CUDA(cudaMemcpyAsync(tcol.data(), z->dT, 8 * (i + 1), cudaMemcpyDeviceToHost, z->st));
     SFCI_CUDA(cudaMemcpyAsync(scol.data(), z->dS, 8 * (i + 1), cudaMemcpyDeviceToHost, z->st));
-    SFCI_CUDA(cudaMemcpyAsync(&hscreened, z->screened, 8, cudaMemcpyDeviceToHost, z->st));
     SFCI_CUDA(cudaStreamSynchronize(z->st));
     for (int j = 0; j <= i; ++j) {
         z->T[size_t(j) * NL + i] = tcol[j];
@@ -405,7 +586,7 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
     info->cycle = z->cycle;
     info->index = i;
     info->n_in = n_in;
-    info->n_sigma = (long long)(hcount - hscreened);
+    info->n_sigma = (long long)n_live;
     const double a = tcol[i], b = i > 0 ? tcol[i - 1] : 0.0;
     info->a = a;
     info->b = b;
@@ -413,16 +594,62 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
 
     bool last = (i == NL - 1) || (z->p.max_iter > 0 && z->iter >= z->p.max_iter);
     if (!last) {
-        // u = sigma_i - a w_i - b w_{i-1}  (Eq. 10), then Eq. 11
-        SFCI_CUDA(table_axpy(t, z->wr[i], z->wc[i], n_in, nullptr, a, -1.0, z->st));
-        if (i > 0) SFCI_CUDA(table_axpy(t, z->wr[i - 1], z->wc[i - 1], z->wn[i - 1], nullptr, b, -1.0, z->st));
+        // u = sigma_i - a w_i - b w_{i-1} on the support of w_i and w_{i-1} (Eq. 10);
+        // elsewhere u = sigma_i, already streamed
+        const VecRef wi = vr[i];
+        const VecRef wm = i > 0 ? vr[i - 1] : VecRef{nullptr, nullptr, 0};
+        unsigned long long *skey = static_cast<unsigned long long *>(z->sig_key.p);
+        double *sval = static_cast<double *>(z->sig_val.p);
+        SFCI_CUDA(launch_u_entries(wi, z->sigw[i], wm, i > 0 ? z->sigw[i - 1] : nullptr, a, b, skey, sval,
+                                   n_stream, z->sig_cap, z->hist, z->msumsq, z->mstatus, z->st));
+        const long long n_items = (long long)n_stream + wi.n + wm.n;
+        // Eq. 11: top-N_d of u
+        const long long cand_cap = std::max<long long>(4 * z->nkeep, 1 << 22);
+        sfci_status rs;
+        if ((rs = ensure(z->cand_key, size_t(cand_cap) * 8, z->st, "candidates"))) return rs;
+        if ((rs = ensure(z->cand_val, size_t(cand_cap) * 8, z->st, "candidates"))) return rs;
+        z->cand_cap = cand_cap;
+        Items it{skey, sval, 1, n_items};
+        SplitResult res{};
+        SFCI_CUDA(select_split(it, z->nkeep, z->hist, z->wr[i + 1], z->wc[i + 1], z->ndev,
+                               static_cast<unsigned long long *>(z->cand_key.p),
+                               static_cast<double *>(z->cand_val.p), cand_cap, z->cand_n,
+                               z->scratch + z->off_sel, z->sel_bytes, &res, z->st));
+        unsigned long long kept = std::min<unsigned long long>(res.n_out, (unsigned long long)z->nkeep);
+        if (!res.done && !res.all) {
+            unsigned long long n2 = 0;
+            if ((long long)res.n_cand > cand_cap) {  // the picked bin is too crowded: exact select over all
+                SFCI_CUDA(select_topk(it, z->nkeep, z->wr[i + 1], z->wc[i + 1], z->total, nullptr, nullptr,
+                                      z->scratch + z->off_sel, z->sel_bytes, z->st));
+                kept = 0;
+            } else {
+                Items ci{static_cast<const unsigned long long *>(z->cand_key.p),
+                         static_cast<const double *>(z->cand_val.p), 1, (long long)res.n_cand};
+                SFCI_CUDA(select_topk(ci, (long long)res.need, z->wr[i + 1] + kept, z->wc[i + 1] + kept,
+                                      z->total, nullptr, nullptr, z->scratch + z->off_sel, z->sel_bytes,
+                                      z->st));
+            }
+            SFCI_CUDA(cudaMemcpyAsync(&n2, z->total, 8, cudaMemcpyDeviceToHost, z->st));
+            SFCI_CUDA(cudaStreamSynchronize(z->st));
+            kept = std::min<unsigned long long>(kept + n2, (unsigned long long)z->nkeep);
+        }
         double usq = 0.0;
-        unsigned long long utot = 0;
-        sfci_status rs = table_topk(z, cap, i + 1, &usq, &utot);
-        if (rs != SFCI_OK) return rs;
+        int hs = 0;
+        SFCI_CUDA(cudaMemcpyAsync(z->ndev, &kept, 8, cudaMemcpyHostToDevice, z->st));
+        SFCI_CUDA(sort_pairs(z->wr[i + 1], z->wc[i + 1], z->nkeep, z->ndev, key_bits(d.dim),
+                             z->scratch + z->off_sort, z->st));
+        SFCI_CUDA(normalize_vec(z->wc[i + 1], z->nkeep, z->ndev, z->scratch + z->off_norm, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(&usq, z->msumsq, 8, cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(&hs, z->mstatus, 4, cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaStreamSynchronize(z->st));
+        if (hs & 8) {
+            set_error("sigma output buffer overflowed while appending u");
+            return SFCI_E_CAPACITY;
+        }
+        z->wn[i + 1] = (long long)kept;
         const double unorm = std::sqrt(usq);
         info->u_norm = unorm;
-        if (unorm < 1e-14 * std::fabs(a) || utot == 0) {
+        if (unorm < 1e-14 * std::fabs(a) || res.total == 0) {
             last = true;
             info->breakdown = 1;
         } else {

@@ -1,0 +1,539 @@
+// The merge of sigma's intermediate elements (Sec. 2.2, step 2), bucketed for
+// GB300.
+//
+// The paper spreads intermediate elements over buckets by index range so that
+// cores merge buckets independently (Sec. 2.2, Fig. 1).  Here the emit kernel
+// appends every element to one of 2^log2B hash buckets (one L2 counter atomic
+// and one 16-byte store per element; bucket tails stay in L2 until their
+// sectors fill, so HBM sees full-sector writes).  Each bucket holds ~2k
+// elements, so one CTA merges a bucket in a shared-memory hash table and
+// streams the distinct entries out: sigma costs one sequential write and one
+// sequential read of the elements instead of a random read-modify-write per
+// element.  A bucket whose counter passes its capacity (one target reached
+// from very many sources) spills into an overflow list that is sorted by
+// bucket before the merge.  When the elements would not fit in memory, the
+// bucket range is processed in passes, each re-enumerating the sources and
+// keeping only its own buckets.
+//
+// The Lanczos quantities are folded into the merge so that sigma is never
+// searched: "probes" (rank k, vector j, position) for every entry of the basis
+// vectors w_0..w_i are sorted into the same buckets; the merge of a bucket looks
+// each probe up in shared memory and records sigma_k next to w_j's entry.  The
+// entries of w_i and w_{i-1} are left out of the streamed output; their
+// u = sigma - a w_i - b w_{i-1} values are formed later from the recorded
+// sigma_k (Eq. 10).  The streamed output and the u entries feed a top-k whose
+// first 12-bit histogram is accumulated by the merge itself.
+#include "sfci_internal.cuh"
+
+namespace sfci {
+namespace {
+
+constexpr int kMT = 256;             // merge CTA threads
+constexpr int kPre = 8;              // elements each thread loads before inserting
+constexpr int kBins = 4096;
+
+template <int kSlots>
+__device__ __forceinline__ unsigned smem_slot(unsigned long long key, int log2B) {
+    return (unsigned)(mix64(key) >> (64 - log2B - 13)) & (kSlots - 1);
+}
+
+__device__ __forceinline__ unsigned top12_bin(double v) {
+    const unsigned long long mag = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    return (unsigned)((0x7fffffffffffffffull - mag) >> 51);
+}
+
+// ------------------------------------------------------------- scan
+
+// exclusive scan of unsigned 32-bit counts into 64-bit offsets, m entries,
+// out[m] = total; three kernels (block sums, scan of sums, block scans)
+__global__ void scan_sums_kernel(const unsigned *in, long long m, unsigned long long *bsum) {
+    __shared__ unsigned long long w[32];
+    const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+    unsigned long long v = i < m ? in[i] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned long long x = w[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        if (threadIdx.x == 0) bsum[blockIdx.x] = x;
+    }
+}
+
+__global__ void scan_top_kernel(unsigned long long *bsum, long long nb) {
+    // one block: exclusive scan of nb block sums in place
+    __shared__ unsigned long long carry, w[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (long long b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const long long i = b0 + threadIdx.x;
+        const unsigned long long v = i < nb ? bsum[i] : 0;
+        unsigned long long x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) w[wp] = x;
+        __syncthreads();
+        if (wp == 0) {
+            const unsigned long long s = w[lane];
+            unsigned long long t = s;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(kFull, t, o);
+                if (lane >= o) t += y;
+            }
+            w[lane] = t - s;
+        }
+        __syncthreads();
+        const unsigned long long ex = carry + w[wp] + x - v;
+        if (i < nb) bsum[i] = ex;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = ex + v;
+        __syncthreads();
+    }
+}
+
+__global__ void scan_block_kernel(const unsigned *in, long long m, const unsigned long long *bsum,
+                                  unsigned long long *out) {
+    __shared__ unsigned long long w[32];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+    const unsigned long long v = i < m ? in[i] : 0;
+    unsigned long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) w[wp] = x;
+    __syncthreads();
+    if (wp == 0) {
+        const unsigned long long s = w[lane];
+        unsigned long long t = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, t, o);
+            if (lane >= o) t += y;
+        }
+        w[lane] = t - s;
+    }
+    __syncthreads();
+    const unsigned long long ex = bsum[blockIdx.x] + w[wp] + x - v;
+    if (i < m) out[i] = ex;
+    if (i == m - 1) out[m] = ex + v;
+}
+
+// ------------------------------------------------------------- overflow
+
+// overflow elements per bucket of the pass = max(count - cap, 0)
+__global__ void ovf_counts_kernel(const unsigned *count, unsigned lo, unsigned nb, unsigned cap,
+                                  unsigned *ovc) {
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        const unsigned c = count[lo + b];
+        ovc[b] = c > cap ? c - cap : 0u;
+    }
+}
+
+__global__ void ovf_scatter_kernel(const Slot *ovf, const unsigned long long *ovf_n, long long ovf_cap,
+                                   int log2B, unsigned lo, const unsigned long long *off,
+                                   unsigned *fill, Slot *out) {
+    long long n = (long long)*ovf_n;
+    if (n > ovf_cap) n = ovf_cap;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const ulonglong2 e = reinterpret_cast<const ulonglong2 *>(ovf)[i];
+        const unsigned b = bucket_of(e.x, log2B) - lo;
+        const unsigned long long pos = off[b] + atomicAdd(&fill[b], 1u);
+        // offsets count every overflowing element; a truncated list (status
+        // bit 1, the sigma is redone) must not write past its end
+        if ((long long)pos < ovf_cap) reinterpret_cast<ulonglong2 *>(out)[pos] = e;
+    }
+}
+
+// ------------------------------------------------------------- probes
+
+__global__ void probe_count_kernel(VecPackRef vp, int nvec, int log2B, unsigned *pcount) {
+    for (int j = 0; j < nvec; ++j) {
+        const VecRef w = vp.v[j];
+        for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < w.n;
+             k += (long long)gridDim.x * blockDim.x)
+            atomicAdd(&pcount[bucket_of(w.rank[k], log2B)], 1u);
+    }
+}
+
+__global__ void probe_scatter_kernel(VecPackRef vp, int nvec, int log2B,
+                                     const unsigned long long *poff, unsigned *pfill, Probe *out) {
+    for (int j = 0; j < nvec; ++j) {
+        const VecRef w = vp.v[j];
+        for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < w.n;
+             k += (long long)gridDim.x * blockDim.x) {
+            const unsigned long long key = w.rank[k];
+            const unsigned b = bucket_of(key, log2B);
+            const unsigned long long pos = poff[b] + atomicAdd(&pfill[b], 1u);
+            Probe p;
+            p.key = key;
+            p.where = ((unsigned long long)j << 40) | (unsigned long long)k;
+            out[pos] = p;
+        }
+    }
+}
+
+// ------------------------------------------------------------- merge
+
+// One CTA merges one bucket at a time (dynamic queue) in a shared-memory hash
+// table.  Every thread first loads up to kPre of the bucket's elements into
+// registers (independent loads in flight together), then inserts them; slots
+// taken for the first time are listed, so clearing and streaming out touch only
+// the occupied slots.
+template <int kSlots>
+__global__ void __launch_bounds__(kMT)
+merge_kernel(MergeArgs A) {
+    extern __shared__ __align__(16) unsigned char msm[];
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(msm);
+    double *vals = reinterpret_cast<double *>(keys + kSlots);
+    unsigned *hist = reinterpret_cast<unsigned *>(vals + kSlots);
+    unsigned short *occ = reinterpret_cast<unsigned short *>(hist + kBins);
+    unsigned char *flag = reinterpret_cast<unsigned char *>(occ + kSlots);
+    __shared__ unsigned cur, n_occ;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool screen = A.eps > 0.0;
+    for (int b = tid; b < kBins; b += kMT) hist[b] = 0;
+    for (int sl = tid; sl < kSlots; sl += kMT) keys[sl] = kEmpty, vals[sl] = 0.0, flag[sl] = 0;
+    if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u);
+    double sq = 0.0;
+    unsigned long long n_live = 0;
+    __syncthreads();
+    for (;;) {
+        const unsigned bi = cur;  // bucket index within the pass
+        if (bi >= A.hi - A.lo) break;
+        const unsigned b = A.lo + bi;
+        const unsigned cnt = A.count[b];
+        const unsigned n_main = cnt < A.cap ? cnt : A.cap;
+        unsigned long long o0 = A.ovf_off[bi], o1 = A.ovf_off[bi + 1];
+        if (o1 > (unsigned long long)A.ovf_cap) o1 = (unsigned long long)A.ovf_cap;  // truncated list
+        if (o0 > o1) o0 = o1;
+        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(A.elem) + size_t(bi) * A.cap;
+        const ulonglong2 *ovs = reinterpret_cast<const ulonglong2 *>(A.ovf_sorted) + o0;
+        const unsigned total = n_main + (unsigned)(o1 - o0);
+        for (unsigned e0 = 0; e0 < total; e0 += kMT * kPre) {
+            ulonglong2 x[kPre];
+#pragma unroll
+            for (int k = 0; k < kPre; ++k) {
+                const unsigned e = e0 + k * kMT + tid;
+                x[k] = make_ulonglong2(kEmpty, 0ull);
+                if (e < total) x[k] = e < n_main ? src[e] : ovs[e - n_main];
+            }
+#pragma unroll
+            for (int k = 0; k < kPre; ++k) {
+                const unsigned long long key = x[k].x;
+                if (key == kEmpty) continue;
+                unsigned h = smem_slot<kSlots>(key, A.log2B);
+                int probe = 0;
+                for (; probe < kSlots; ++probe) {
+                    const unsigned long long c = keys[h];
+                    if (c == key) break;
+                    if (c == kEmpty) {
+                        const unsigned long long old = atomicCAS(&keys[h], kEmpty, key);
+                        if (old == kEmpty) {
+                            occ[atomicAdd(&n_occ, 1u)] = (unsigned short)h;
+                            break;
+                        }
+                        if (old == key) break;
+                    }
+                    h = (h + 1) & (kSlots - 1);
+                }
+                if (probe < kSlots) atomicAdd(&vals[h], __longlong_as_double((long long)x[k].y));
+                else atomicOr(A.status, 4);
+            }
+        }
+        __syncthreads();
+        // probes: record sigma at the basis-vector entries
+        const unsigned long long p0 = A.probe_off[b], p1 = A.probe_off[b + 1];
+        for (unsigned long long p = p0 + tid; p < p1; p += kMT) {
+            const Probe pr = A.probes[p];
+            unsigned h = smem_slot<kSlots>(pr.key, A.log2B);
+            int found = -1;
+            for (int q = 0; q < kSlots; ++q) {
+                const unsigned long long c = keys[h];
+                if (c == pr.key) {
+                    found = (int)h;
+                    break;
+                }
+                if (c == kEmpty) break;
+                h = (h + 1) & (kSlots - 1);
+            }
+            double sv = found >= 0 ? vals[found] : 0.0;
+            if (screen && fabs(sv) < A.eps) sv = 0.0;  // screened entries count as absent
+            const int j = (int)(pr.where >> 40);
+            const long long k = (long long)(pr.where & ((1ull << 40) - 1));
+            A.sigw[j][k] = sv;
+            if (found >= 0 && (j == A.ja || j == A.jb)) flag[found] = 1;
+        }
+        __syncthreads();
+        // stream the occupied slots out (u = sigma there), histogram of |u|,
+        // and clear them for the next bucket
+        const unsigned nocc = n_occ;
+        for (unsigned t0 = 0; t0 < nocc; t0 += kMT) {
+            const unsigned t = t0 + tid;
+            unsigned long long key = kEmpty;
+            double v = 0.0;
+            bool live = false, w = false;
+            if (t < nocc) {
+                const unsigned sl = occ[t];
+                key = keys[sl];
+                v = vals[sl];
+                live = !(screen && fabs(v) < A.eps);
+                w = live && !flag[sl];
+                keys[sl] = kEmpty, vals[sl] = 0.0, flag[sl] = 0;
+            }
+            n_live += live;
+            const unsigned bal = __ballot_sync(kFull, w);
+            unsigned long long base = 0;
+            if (lane == 0 && bal) base = atomicAdd(A.out_n, (unsigned long long)__popc(bal));
+            base = __shfl_sync(kFull, base, 0);
+            if (w) {
+                const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
+                if ((long long)pos < A.out_cap) {
+                    A.out_key[pos] = key;
+                    A.out_val[pos] = v;
+                } else {
+                    atomicOr(A.status, 8);
+                }
+                const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
+                if (vb << 1) {  // non-zero
+                    atomicAdd(&hist[(unsigned)((0x7fffffffffffffffull - (vb & 0x7fffffffffffffffull)) >> 51)], 1u);
+                    sq = __fma_rn(v, v, sq);
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u);
+        __syncthreads();
+    }
+    for (int b = tid; b < kBins; b += kMT)
+        if (hist[b]) atomicAdd(&A.hist[b], (unsigned long long)hist[b]);
+    for (int o = 16; o > 0; o >>= 1) {
+        sq += __shfl_xor_sync(kFull, sq, o);
+        n_live += __shfl_xor_sync(kFull, n_live, o);
+    }
+    if (lane == 0) {
+        atomicAdd(A.sumsq, sq);
+        atomicAdd(A.n_live, n_live);
+    }
+}
+
+constexpr size_t merge_smem(int slots) { return size_t(slots) * (8 + 8 + 2 + 1) + size_t(kBins) * 4; }
+
+// ------------------------------------------------------------- u entries
+
+// u on the support of w_i (and w_{i-1}): u_k = sigma_k - a w_i[k] - b w_{i-1}[k]
+// (Eq. 10), appended after the streamed entries; entries of w_{i-1} that w_i
+// also holds are written as empty keys.
+__global__ void u_entries_kernel(VecRef wi, const double *sig_i, VecRef wm, const double *sig_m,
+                                 double a, double b, unsigned long long *out_key, double *out_val,
+                                 unsigned long long base_n, long long out_cap,
+                                 unsigned long long *hist, double *sumsq, int *status) {
+    double sq = 0.0;
+    const long long total = wi.n + wm.n;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        unsigned long long key;
+        double u;
+        bool valid = true;
+        if (t < wi.n) {
+            key = wi.rank[t];
+            u = __dsub_rn(sig_i[t], __dmul_rn(a, wi.coef[t]));
+            // w_{i-1} entry with the same rank
+            long long lo = 0, hi = wm.n;
+            while (lo < hi) {
+                const long long mid = lo + ((hi - lo) >> 1);
+                if (wm.rank[mid] < key) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < wm.n && wm.rank[lo] == key) u = __dsub_rn(u, __dmul_rn(b, wm.coef[lo]));
+        } else {
+            const long long k = t - wi.n;
+            key = wm.rank[k];
+            long long lo = 0, hi = wi.n;
+            while (lo < hi) {
+                const long long mid = lo + ((hi - lo) >> 1);
+                if (wi.rank[mid] < key) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < wi.n && wi.rank[lo] == key) valid = false;
+            u = __dsub_rn(sig_m[k], __dmul_rn(b, wm.coef[k]));
+        }
+        const unsigned long long pos = base_n + (unsigned long long)t;
+        if ((long long)pos >= out_cap) {
+            atomicOr(status, 8);
+            continue;
+        }
+        out_key[pos] = valid ? key : kEmpty;
+        out_val[pos] = valid ? u : 0.0;
+        if (valid && u != 0.0) {
+            atomicAdd(&hist[top12_bin(u)], 1ull);
+            sq = __fma_rn(u, u, sq);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
+    if ((threadIdx.x & 31) == 0 && sq != 0.0) atomicAdd(sumsq, sq);
+}
+
+// <w_j | sigma> from the recorded sigma at w_j's entries: fixed grid, fixed order
+constexpr int kDotBlocks = 304;
+
+__global__ void aligned_dots_kernel(VecPackRef vp, SigPack sp, double *partial) {
+    __shared__ double sh[8];
+    const int j = blockIdx.y;
+    const VecRef w = vp.v[j];
+    const double *sg = sp.p[j];
+    double acc = 0.0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < w.n;
+         k += (long long)gridDim.x * blockDim.x)
+        acc = __fma_rn(w.coef[k], sg[k], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r += sh[q];
+        partial[(size_t)j * gridDim.x + blockIdx.x] = r;
+    }
+}
+
+__global__ void aligned_finish_kernel(const double *partial, int np, double *out) {
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int k = 0; k < np; ++k) r += partial[(size_t)blockIdx.x * np + k];
+        out[blockIdx.x] = r;
+    }
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+unsigned grid_for(long long work, int per_sm) {
+    long long g = (work + 255) / 256;
+    const long long c = (long long)sm_count() * per_sm;
+    if (g > c) g = c;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+}  // namespace
+
+size_t scan_ws_bytes(long long m) {
+    const long long nb = (m + 1023) / 1024;
+    return size_t(nb > 0 ? nb : 1) * 8;
+}
+
+cudaError_t exclusive_scan(const unsigned *in, long long m, unsigned long long *out, void *ws,
+                           cudaStream_t st) {
+    if (m <= 0) return cudaMemsetAsync(out, 0, 8, st);
+    const long long nb = (m + 1023) / 1024;
+    unsigned long long *bsum = static_cast<unsigned long long *>(ws);
+    count_launch();
+    scan_sums_kernel<<<(unsigned)nb, 1024, 0, st>>>(in, m, bsum);
+    count_launch();
+    scan_top_kernel<<<1, 1024, 0, st>>>(bsum, nb);
+    count_launch();
+    scan_block_kernel<<<(unsigned)nb, 1024, 0, st>>>(in, m, bsum, out);
+    return cudaGetLastError();
+}
+
+cudaError_t sort_overflow(const unsigned *count, unsigned lo, unsigned nb, unsigned cap,
+                          const Slot *ovf, const unsigned long long *ovf_n, long long ovf_cap,
+                          int log2B, unsigned *tmp_counts, unsigned long long *off, void *scan_ws,
+                          Slot *out, cudaStream_t st) {
+    count_launch();
+    ovf_counts_kernel<<<grid_for(nb, 8), 256, 0, st>>>(count, lo, nb, cap, tmp_counts);
+    cudaError_t e = exclusive_scan(tmp_counts, nb, off, scan_ws, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(tmp_counts, 0, size_t(nb) * 4, st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    ovf_scatter_kernel<<<grid_for(ovf_cap < (1 << 24) ? ovf_cap : (1 << 24), 8), 256, 0, st>>>(
+        ovf, ovf_n, ovf_cap, log2B, lo, off, tmp_counts, out);
+    return cudaGetLastError();
+}
+
+cudaError_t sort_probes(const VecRef *vecs, int nvec, int log2B, unsigned *pcount,
+                        unsigned long long *poff, void *scan_ws, Probe *out, cudaStream_t st) {
+    const unsigned long long B = 1ull << log2B;
+    VecPackRef vp{};
+    long long tot = 0;
+    for (int j = 0; j < nvec; ++j) vp.v[j] = vecs[j], tot += vecs[j].n;
+    cudaError_t e = cudaMemsetAsync(pcount, 0, B * 4, st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    probe_count_kernel<<<grid_for(tot / (nvec > 0 ? nvec : 1) + 1, 8), 256, 0, st>>>(vp, nvec, log2B, pcount);
+    e = exclusive_scan(pcount, (long long)B, poff, scan_ws, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(pcount, 0, B * 4, st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    probe_scatter_kernel<<<grid_for(tot / (nvec > 0 ? nvec : 1) + 1, 8), 256, 0, st>>>(
+        vp, nvec, log2B, poff, pcount, out);
+    return cudaGetLastError();
+}
+
+template <int kSlots>
+cudaError_t launch_merge_t(const MergeArgs &A, cudaStream_t st) {
+    const size_t smem = merge_smem(kSlots);
+    cudaError_t e = cudaFuncSetAttribute(merge_kernel<kSlots>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, merge_kernel<kSlots>, kMT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const long long nb = (long long)(A.hi - A.lo);
+    long long grid = (long long)sm_count() * per_sm;
+    if (grid > nb) grid = nb;
+    if (grid < 1) return cudaSuccess;
+    count_launch();
+    merge_kernel<kSlots><<<(unsigned)grid, kMT, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const MergeArgs &A, int slots, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(A.queue, 0, 4, st);
+    if (e != cudaSuccess) return e;
+    if (slots <= 2048) return launch_merge_t<2048>(A, st);
+    if (slots <= 4096) return launch_merge_t<4096>(A, st);
+    return launch_merge_t<8192>(A, st);
+}
+
+cudaError_t launch_u_entries(VecRef wi, const double *sig_i, VecRef wm, const double *sig_m,
+                             double a, double b, unsigned long long *out_key, double *out_val,
+                             unsigned long long base_n, long long out_cap, unsigned long long *hist,
+                             double *sumsq, int *status, cudaStream_t st) {
+    const long long total = wi.n + wm.n;
+    if (total <= 0) return cudaSuccess;
+    count_launch();
+    u_entries_kernel<<<grid_for(total, 8), 256, 0, st>>>(wi, sig_i, wm, sig_m, a, b, out_key, out_val,
+                                                         base_n, out_cap, hist, sumsq, status);
+    return cudaGetLastError();
+}
+
+size_t aligned_dots_ws_bytes(int nvec) { return size_t(nvec > 0 ? nvec : 1) * kDotBlocks * 8; }
+
+cudaError_t aligned_dots(const VecRef *vecs, double *const *sig, int nvec, double *out_dev, void *ws,
+                         cudaStream_t st) {
+    if (nvec <= 0) return cudaSuccess;
+    VecPackRef vp{};
+    SigPack sp{};
+    for (int j = 0; j < nvec; ++j) vp.v[j] = vecs[j], sp.p[j] = sig[j];
+    double *partial = static_cast<double *>(ws);
+    count_launch();
+    aligned_dots_kernel<<<dim3(kDotBlocks, nvec), 256, 0, st>>>(vp, sp, partial);
+    count_launch();
+    aligned_finish_kernel<<<nvec, 32, 0, st>>>(partial, kDotBlocks, out_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace sfci

@@ -36,7 +36,7 @@ struct SelState {
 };
 
 struct SelLayout {
-    size_t state, hist, n_gather, bytes;
+    size_t state, hist, n_gather, result, bytes;
 };
 
 inline size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -47,6 +47,7 @@ SelLayout sel_layout() {
     L.state = o, o = a256(o + sizeof(SelState));
     L.hist = o, o = a256(o + sizeof(unsigned long long) * kBins);
     L.n_gather = o, o = a256(o + sizeof(unsigned long long));
+    L.result = o, o = a256(o + sizeof(SplitResult));
     L.bytes = o;
     return L;
 }
@@ -245,6 +246,87 @@ __global__ void sel_stats_kernel(const SelState *s, double *sumsq_out, unsigned 
     if (threadIdx.x == 0) {
         if (sumsq_out) *sumsq_out = s->sumsq;
         if (total_out) *total_out = s->total;
+    }
+}
+
+__global__ void sel_load_hist_kernel(SelState *s, unsigned long long k, const unsigned long long *h0,
+                                     unsigned long long *hist, unsigned long long *n_out,
+                                     unsigned long long *cand_n) {
+    __shared__ unsigned long long part[kT];
+    unsigned long long t = 0;
+    for (int b = threadIdx.x; b < kBins; b += blockDim.x) {
+        hist[b] = h0[b];
+        t += h0[b];
+    }
+    part[threadIdx.x] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tot = 0;
+        for (int q = 0; q < kT; ++q) tot += part[q];
+        s->pfx_hi = s->pfx_lo = s->mask_hi = s->mask_lo = 0ull;
+        s->need = k;
+        s->total = tot;
+        s->done = (k == 0);
+        s->all = 0;
+        s->pass = 0;
+        s->sumsq = 0.0;
+        *n_out = 0;
+        *cand_n = 0;
+    }
+}
+
+// one pass: items of a smaller first digit than the picked bin -> out; of the
+// picked bin -> cand (or out, when the bin is taken whole)
+__global__ void sel_split_kernel(Items it, const SelState *s, unsigned long long *out_key,
+                                 double *out_val, long long out_cap, unsigned long long *n_out,
+                                 unsigned long long *cand_key, double *cand_val, long long cand_cap,
+                                 unsigned long long *cand_n) {
+    const int lane = threadIdx.x & 31;
+    const bool all = s->all, done = s->done;
+    const bool none = !all && s->mask_hi == 0;  // k == 0
+    const unsigned b0 = (unsigned)(s->pfx_hi >> 51);
+    for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < it.n;
+         i0 += (long long)gridDim.x * blockDim.x) {
+        const long long i = i0 + threadIdx.x;
+        int dest = 0;  // 0 none, 1 out, 2 cand
+        unsigned long long key = 0, vb = 0;
+        if (i < it.n && !none) {
+            key = it.key[(size_t)i * it.stride];
+            vb = (unsigned long long)__double_as_longlong(it.val[(size_t)i * it.stride]);
+            if (item_valid(key, vb)) {
+                const unsigned d0 = (unsigned)((0x7fffffffffffffffull - (vb & 0x7fffffffffffffffull)) >> 51);
+                if (all || d0 < b0 || (done && d0 == b0)) dest = 1;
+                else if (d0 == b0) dest = 2;
+            }
+        }
+        const unsigned bo = __ballot_sync(kFull, dest == 1), bc = __ballot_sync(kFull, dest == 2);
+        unsigned long long base_o = 0, base_c = 0;
+        if (lane == 0) {
+            if (bo) base_o = atomicAdd(n_out, (unsigned long long)__popc(bo));
+            if (bc) base_c = atomicAdd(cand_n, (unsigned long long)__popc(bc));
+        }
+        base_o = __shfl_sync(kFull, base_o, 0);
+        base_c = __shfl_sync(kFull, base_c, 0);
+        const unsigned lt = (1u << lane) - 1u;
+        if (dest == 1) {
+            const unsigned long long pos = base_o + __popc(bo & lt);
+            if ((long long)pos < out_cap) out_key[pos] = key, out_val[pos] = __longlong_as_double((long long)vb);
+        } else if (dest == 2) {
+            const unsigned long long pos = base_c + __popc(bc & lt);
+            if ((long long)pos < cand_cap) cand_key[pos] = key, cand_val[pos] = __longlong_as_double((long long)vb);
+        }
+    }
+}
+
+__global__ void sel_split_result_kernel(const SelState *s, const unsigned long long *n_out,
+                                        const unsigned long long *cand_n, SplitResult *r) {
+    if (threadIdx.x == 0) {
+        r->n_out = *n_out;
+        r->n_cand = *cand_n;
+        r->need = s->need;
+        r->total = s->total;
+        r->all = s->all;
+        r->done = s->done;
     }
 }
 
@@ -448,6 +530,32 @@ cudaError_t select_topk(Items it, long long k, unsigned long long *out_key, doub
         sel_stats_kernel<<<1, 32, 0, st>>>(s, sumsq_dev, total_dev);
     }
     return cudaGetLastError();
+}
+
+cudaError_t select_split(Items it, long long k, const unsigned long long *hist0,
+                         unsigned long long *out_key, double *out_val, unsigned long long *n_out_dev,
+                         unsigned long long *cand_key, double *cand_val, long long cand_cap,
+                         unsigned long long *cand_n, void *ws, size_t ws_bytes, SplitResult *res_host,
+                         cudaStream_t st) {
+    const SelLayout L = sel_layout();
+    if (ws_bytes < L.bytes) return cudaErrorInvalidValue;
+    char *base = static_cast<char *>(ws);
+    SelState *s = reinterpret_cast<SelState *>(base + L.state);
+    unsigned long long *hist = reinterpret_cast<unsigned long long *>(base + L.hist);
+    SplitResult *r = reinterpret_cast<SplitResult *>(base + L.result);
+    count_launch();
+    sel_load_hist_kernel<<<1, kT, 0, st>>>(s, (unsigned long long)(k < 0 ? 0 : k), hist0, hist,
+                                           n_out_dev, cand_n);
+    count_launch();
+    sel_pick_kernel<<<1, kT, 0, st>>>(s, hist, 0);
+    count_launch();
+    sel_split_kernel<<<grid_for(it.n, 8), kT, 0, st>>>(it, s, out_key, out_val, k, n_out_dev,
+                                                       cand_key, cand_val, cand_cap, cand_n);
+    count_launch();
+    sel_split_result_kernel<<<1, 32, 0, st>>>(s, n_out_dev, cand_n, r);
+    cudaError_t e = cudaMemcpyAsync(res_host, r, sizeof(SplitResult), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
 }
 
 size_t sort_pairs_bytes(long long cap) {
