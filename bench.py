@@ -222,8 +222,13 @@ def run_ours(a):
     stream = torch.cuda.current_stream()
     lz = sf.Lanczos(gsys, np.array([0], dtype=np.uint64), np.array([1.0]), a.nkeep, a.nlanczos,
                     table_capacity=a.table_capacity, bucket_elems=a.bucket_elems, stream=stream)
+    def brief(i):
+        return {k: i[k] for k in ("n_in", "n_sigma", "n_passes", "ms_plan", "ms_emit", "ms_merge",
+                                  "ms_topk", "ms_step")}
+
+    warm = []
     for _ in range(a.warmup):
-        lz.step()
+        warm.append(brief(lz.step()))
     barrier()
     launches0 = sf.kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -266,6 +271,10 @@ def run_ours(a):
                 "model": f"{BYTES_PER_ELEMENT} B per connected element (16 B written by emit, "
                          f"16 B read by merge)",
                 "ms_per_launch": ms_sig, "ms_emit": ms_emit, "ms_merge": ms_merge,
+                "ms_plan_host": statistics.mean(i["ms_plan"] for i in infos),
+                "ms_topk": statistics.mean(i["ms_topk"] for i in infos),
+                "passes": max(i["n_passes"] for i in infos),
+                "buckets_log2": max(i["n_buckets_log2"] for i in infos),
                 "elements_per_launch": el_per_launch,
                 "sigma_share_of_step": sum(i["ms_sigma"] for i in infos) / ms}
 
@@ -322,7 +331,8 @@ def run_ours(a):
         "clocks": clk.summary(),
         "detail": {"n_in": infos[-1]["n_in"], "n_sigma": infos[-1]["n_sigma"],
                    "elements_per_step": el_per_launch, "lambda_min": last_lambda[-1] if last_lambda else None,
-                   "ms_sigma_mean": ms_sig},
+                   "ms_sigma_mean": ms_sig,
+                   "warmup_steps": warm, "timed_steps": [brief(i) for i in infos]},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

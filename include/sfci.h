@@ -174,6 +174,10 @@ typedef struct sfci_step_info {
     double ms_step;    /* device time of the whole step                             */
     double ms_emit;    /* of ms_sigma: the emit kernel (all passes)                 */
     double ms_merge;   /* of ms_sigma: overflow sort + merge kernel (all passes)    */
+    double ms_plan;    /* host time planning the merge buckets and buffers          */
+    double ms_topk;    /* device time of the truncation (u entries, top-k, sort)    */
+    int32_t n_passes;  /* passes over the sources that sigma needed (memory bound)  */
+    int32_t n_buckets_log2; /* ceil(log2(merge buckets))                            */
 } sfci_step_info;
 
 typedef struct sfci_lanczos sfci_lanczos; /* opaque; owns w_0..w_{N_L-1}, T, S, table */

@@ -43,7 +43,9 @@ class StepInfo(C.Structure):
                 ("n_in", C.c_int64), ("n_sigma", C.c_int64), ("n_kept", C.c_int64),
                 ("n_elements", C.c_int64), ("n_psi", C.c_int64),
                 ("ms_sigma", C.c_double), ("ms_step", C.c_double),
-                ("ms_emit", C.c_double), ("ms_merge", C.c_double)]
+                ("ms_emit", C.c_double), ("ms_merge", C.c_double),
+                ("ms_plan", C.c_double), ("ms_topk", C.c_double),
+                ("n_passes", C.c_int32), ("n_buckets_log2", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

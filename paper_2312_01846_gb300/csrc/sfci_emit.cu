@@ -100,48 +100,143 @@ __device__ __forceinline__ bool nonzero(double v) {
     return ((unsigned long long)__double_as_longlong(v) << 1) != 0ull;
 }
 
-__device__ __forceinline__ void bucket_store(const BucketOut &B, unsigned b, unsigned pos,
-                                             unsigned long long tg, double v) {
-    const ulonglong2 sl = make_ulonglong2(tg, (unsigned long long)__double_as_longlong(v));
-    if (pos < B.cap) {
-        reinterpret_cast<ulonglong2 *>(B.elem)[size_t(b - B.lo) * B.cap + pos] = sl;
-    } else {
-        const unsigned long long q = atomicAdd(B.ovf_n, 1ull);
-        if ((long long)q < B.ovf_cap) reinterpret_cast<ulonglong2 *>(B.ovf)[q] = sl;
-        else atomicOr(B.status, 2);
+constexpr int kU = 4;  // elements each lane carries per reservation round
+
+__device__ __forceinline__ bool in_pass(const BucketOut &B, unsigned b) { return b >= B.lo && b < B.hi; }
+
+// can any bucket of row ha be in this pass?  (row mode: a row's buckets are
+// contiguous; hash mode: always)
+__device__ __forceinline__ bool row_in_pass(const BucketOut &B, unsigned long long ha) {
+    if (!B.bk.rowmap) return true;
+    const unsigned long long m = __ldg(&B.bk.rowmap[ha]);
+    const unsigned ns = (unsigned)m, first = (unsigned)(m >> 32);
+    return ns > 0 && first < B.hi && first + ns > B.lo;
+}
+
+// Up to kU elements per lane (ok[k]) are appended to their buckets: the lanes
+// of the warp that share a bucket reserve their slots with one atomic, issued
+// for all k before any result is used, and write one run.
+__device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, const unsigned *bk,
+                                            const unsigned long long *tg, const double *v) {
+    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    unsigned peers[kU], base[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) peers[k] = __match_any_sync(kFull, ok[k] ? bk[k] : (0x80000000u | lane));
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+        base[k] = 0;
+        if (ok[k] && (peers[k] & lt) == 0) base[k] = atomicAdd(&B.count[bk[k]], (unsigned)__popc(peers[k]));
+    }
+#pragma unroll
+    for (int k = 0; k < kU; ++k) base[k] = __shfl_sync(kFull, base[k], __ffs(peers[k]) - 1);
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+        if (!ok[k]) continue;
+        const unsigned pos = base[k] + __popc(peers[k] & lt);
+        const unsigned long long o0 = __ldg(&B.bk.boff[bk[k]]), o1 = __ldg(&B.bk.boff[bk[k] + 1]);
+        const ulonglong2 sl = make_ulonglong2(tg[k], (unsigned long long)__double_as_longlong(v[k]));
+        if (pos < o1 - o0) {
+            reinterpret_cast<ulonglong2 *>(B.elem)[o0 - __ldg(&B.bk.boff[B.lo]) + pos] = sl;
+        } else {
+            const unsigned long long q = atomicAdd(B.ovf_n, 1ull);
+            if ((long long)q < B.ovf_cap) reinterpret_cast<ulonglong2 *>(B.ovf)[q] = sl;
+            else atomicOr(B.status, 2);
+        }
     }
 }
 
-constexpr int kU = 4;  // bucket reservations each lane keeps in flight
-
-// Is the element of target rank tg wanted by this launch?  (bucketed merge:
-// only buckets of the current pass)
+// One round of the warp over up to kU elements per lane: element k of this
+// lane targets (ha[k], hb[k]) with unscaled value e[k] (only computed when
+// want[k]); debug and table modes deliver lane by lane.
 template <int kMode>
-__device__ __forceinline__ bool wanted(const EmitOut &o, unsigned long long tg) {
-    if (kMode != kModeBucket) return true;
-    const unsigned b = bucket_of(tg, o.b.log2B);
-    return b >= o.b.lo && b < o.b.hi;
-}
-
-// Deliver element e (unscaled) of source s with coefficient c to its target tg.
-template <int kMode>
-__device__ __forceinline__ void deliver(const EmitOut &o, long long di, long long s,
-                                        unsigned long long tg, double e, double c,
-                                        unsigned &inserted) {
+__device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
+                                           const unsigned long long *ha, const unsigned long long *hb,
+                                           const double *e, const long long *di, long long s, double c,
+                                           unsigned long long cb, unsigned &inserted) {
     if (kMode == kModeDebug) {
-        o.dsrc[di] = s;
-        o.dtgt[di] = tg;
-        o.delem[di] = e;
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            if (want[k]) o.dsrc[di[k]] = s, o.dtgt[di[k]] = ha[k] * cb + hb[k], o.delem[di[k]] = e[k];
         return;
     }
-    const double v = __dmul_rn(e, c);
-    if (!nonzero(v)) return;
     if (kMode == kModeTable) {
-        table_add(o.t, tg, v, inserted);
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            if (!want[k]) continue;
+            const double v = __dmul_rn(e[k], c);
+            if (nonzero(v)) table_add(o.t, ha[k] * cb + hb[k], v, inserted);
+        }
         return;
     }
-    const unsigned b = bucket_of(tg, o.b.log2B);
-    bucket_store(o.b, b, atomicAdd(&o.b.count[b], 1u), tg, v);
+    bool ok[kU];
+    unsigned bk[kU];
+    unsigned long long tg[kU];
+    double v[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+        ok[k] = false;
+        bk[k] = 0;
+        tg[k] = 0;
+        v[k] = 0.0;
+        if (!want[k]) continue;
+        v[k] = __dmul_rn(e[k], c);
+        tg[k] = ha[k] * cb + hb[k];
+        bk[k] = bucket_ab(o.b.bk, ha[k], hb[k]);
+        ok[k] = nonzero(v[k]);
+    }
+    warp_append(o.b, ok, bk, tg, v);
+}
+
+// target in this launch?  (bucket mode: its bucket is in the pass)
+template <int kMode>
+__device__ __forceinline__ bool wanted(const EmitOut &o, unsigned long long ha, unsigned long long hb) {
+    if (kMode != kModeBucket) return true;
+    const unsigned b = bucket_ab(o.b.bk, ha, hb);
+    if (b == kNoBucket) {
+        atomicOr(o.b.status, 16);
+        return false;
+    }
+    return in_pass(o.b, b);
+}
+
+// prefix sums A0 | A1 | A2 over the M - 2 electrons of str left after removing
+// occupied positions io < jo:  A0[m] = sum_{t<=m} C(r_t, t), A1[m] = sum C(r_t, t+1),
+// A2[m] = sum C(r_t, t+2) (every lane of the warp calls it)
+__device__ __forceinline__ void pair_prefix(const unsigned char *occ, int M, int io, int jo,
+                                            const unsigned long long *bt, int ks,
+                                            unsigned long long *pre) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long c0 = 0, c1 = 0, c2 = 0;
+    if (lane < M - 2) {
+        int t = lane;
+        if (t >= io) ++t;
+        if (t >= jo) ++t;
+        const int e = occ[t];
+        c0 = bt[e * ks + lane + 1];
+        c1 = bt[e * ks + lane + 2];
+        c2 = bt[e * ks + lane + 3];
+    }
+    for (int w = 1; w < 32; w <<= 1) {
+        const unsigned long long y0 = __shfl_up_sync(kFull, c0, w);
+        const unsigned long long y1 = __shfl_up_sync(kFull, c1, w);
+        const unsigned long long y2 = __shfl_up_sync(kFull, c2, w);
+        if (lane >= w) c0 += y0, c1 += y1, c2 += y2;
+    }
+    if (lane < M - 2) pre[lane + 1] = c0, pre[64 + lane + 1] = c1, pre[128 + lane + 1] = c2;
+    if (lane == 0) pre[0] = 0, pre[64] = 0, pre[128] = 0;
+    __syncwarp();
+}
+
+// Eq. 12 index of rem | a | b (a < b empty in rem) from the prefix sums: the
+// spectators below a keep their position, those between a and b move up one,
+// those above b move up two
+__device__ __forceinline__ unsigned long long pair_rank(unsigned long long rem, int a, int b, int M,
+                                                        const unsigned long long *pre,
+                                                        const unsigned long long *bt, int ks) {
+    const int q1 = __popcll(rem & ((1ull << a) - 1ull));
+    const int q2 = __popcll(rem & ((1ull << b) - 1ull));
+    return pre[q1] + bt[a * ks + q1 + 1] + pre[64 + q2] - pre[64 + q1] + bt[b * ks + q2 + 2] +
+           pre[128 + (M - 2)] - pre[128 + q2];
 }
 
 template <int kMode>
@@ -203,155 +298,167 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             offB1[y] = unsigned(b * n + j) | (sg << 31);
         }
         __syncwarp();
+        const bool self_row = kMode != kModeBucket || row_in_pass(o.b, hA);
 
-        // diagonal
-        if (lane == 0 && wanted<kMode>(o, r))
-            deliver<kMode>(o, base, s, r, diagonal_element(d, occA, occB), c, inserted);
-        // singles; the element is only evaluated for wanted targets
-        long long off = base + 1;
-        for (int x = lane; x < d.sa; x += 32) {
-            const unsigned long long tg = rankA1[x] * cb + hB;
-            if (!wanted<kMode>(o, tg)) continue;
-            const int io = x / d.va, iv = x - io * d.va;
-            const double F = single_element(d, occA[io], virA[iv], occA, occB, occA, d.na);
-            deliver<kMode>(o, off + x, s, tg, flip(F, offA1[x] >> 31), c, inserted);
+        bool want[kU];
+        unsigned long long ha[kU], hb[kU];
+        double e[kU];
+        long long di[kU];
+#define SFCI_CLEAR()                                      \
+    for (int k = 0; k < kU; ++k) want[k] = false, ha[k] = 0, hb[k] = 0, e[k] = 0.0, di[k] = 0;
+
+        // diagonal (lane 0) and alpha singles
+        for (int x0 = -1; x0 < d.sa; x0 += 32 * kU) {
+            SFCI_CLEAR();
+#pragma unroll
+            for (int k = 0; k < kU; ++k) {
+                const int x = x0 + 32 * k + lane;
+                if (x == -1) {
+                    if (!self_row || !wanted<kMode>(o, hA, hB)) continue;
+                    want[k] = true, ha[k] = hA, hb[k] = hB, di[k] = base;
+                    e[k] = diagonal_element(d, occA, occB);
+                } else if (x >= 0 && x < d.sa) {
+                    if (!wanted<kMode>(o, rankA1[x], hB)) continue;
+                    const int io = x / d.va, iv = x - io * d.va;
+                    const double F = single_element(d, occA[io], virA[iv], occA, occB, occA, d.na);
+                    want[k] = true, ha[k] = rankA1[x], hb[k] = hB, di[k] = base + 1 + x;
+                    e[k] = flip(F, offA1[x] >> 31);
+                }
+            }
+            emit_round<kMode>(o, want, ha, hb, e, di, s, c, cb, inserted);
         }
-        off += d.sa;
-        for (int y = lane; y < d.sb; y += 32) {
-            const unsigned long long tg = hA * cb + rankB1[y];
-            if (!wanted<kMode>(o, tg)) continue;
-            const int jo = y / d.vb, jv = y - jo * d.vb;
-            const double F = single_element(d, occB[jo], virB[jv], occA, occB, occB, d.nb);
-            deliver<kMode>(o, off + y, s, tg, flip(F, offB1[y] >> 31), c, inserted);
+        long long off = base + 1 + d.sa;
+        // beta singles (all in row hA)
+        if (self_row) {
+            for (int y0 = 0; y0 < d.sb; y0 += 32 * kU) {
+                SFCI_CLEAR();
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int y = y0 + 32 * k + lane;
+                    if (y >= d.sb || !wanted<kMode>(o, hA, rankB1[y])) continue;
+                    const int jo = y / d.vb, jv = y - jo * d.vb;
+                    const double F = single_element(d, occB[jo], virB[jv], occA, occB, occB, d.nb);
+                    want[k] = true, ha[k] = hA, hb[k] = rankB1[y], di[k] = off + y;
+                    e[k] = flip(F, offB1[y] >> 31);
+                }
+                emit_round<kMode>(o, want, ha, hb, e, di, s, c, cb, inserted);
+            }
         }
         off += d.sb;
-        // same-spin doubles (i<j) -> (a<b), i->a then j->b.  The index of the
-        // excited string comes from prefix sums over the M-2 spectators r_t:
-        //   A0[m] = sum_{t<=m} C(r_t, t), A1[m] = sum C(r_t, t+1), A2[m] = sum C(r_t, t+2);
-        //   h = A0[q1] + C(a, q1+1) + A1[q2] - A1[q1] + C(b, q2+2) + A2[M-2] - A2[q2]
-        // with q1, q2 the spectators below a and below b (Eq. 12 term by term).
+        // same-spin doubles (i<j) -> (a<b), i->a then j->b; the excited
+        // string's index from the prefix sums (pair_rank)
         for (int spin = 0; spin < 2; ++spin) {
             const unsigned long long str = spin ? beta : alpha;
             const unsigned char *occ = spin ? occB : occA, *vir = spin ? virB : virA;
             const unsigned char *po = spin ? pOB : pOA, *pv = spin ? pVB : pVA;
             const int npo = spin ? d.po_b : d.po_a, npv = spin ? d.pv_b : d.pv_a;
             const int M = spin ? d.nb : d.na;
+            if (spin == 1 && !self_row) {  // beta-beta doubles stay in row hA
+                off += (long long)npo * npv;
+                continue;
+            }
             for (int p = 0; p < npo; ++p) {
                 const int io = po[2 * p], jo = po[2 * p + 1];
                 const int i = occ[io], j = occ[jo];
                 const unsigned long long rem = str ^ (1ull << i) ^ (1ull << j);
-                {
-                    unsigned long long c0 = 0, c1 = 0, c2 = 0;
-                    if (lane < M - 2) {
-                        int t = lane;
-                        if (t >= io) ++t;
-                        if (t >= jo) ++t;
-                        const int e = occ[t];
-                        c0 = bt[e * ks + lane + 1];
-                        c1 = bt[e * ks + lane + 2];
-                        c2 = bt[e * ks + lane + 3];
-                    }
-                    for (int w = 1; w < 32; w <<= 1) {
-                        const unsigned long long y0 = __shfl_up_sync(kFull, c0, w);
-                        const unsigned long long y1 = __shfl_up_sync(kFull, c1, w);
-                        const unsigned long long y2 = __shfl_up_sync(kFull, c2, w);
-                        if (lane >= w) c0 += y0, c1 += y1, c2 += y2;
-                    }
-                    if (lane < M - 2) pre[lane + 1] = c0, pre[64 + lane + 1] = c1, pre[128 + lane + 1] = c2;
-                    if (lane == 0) pre[0] = 0, pre[64] = 0, pre[128] = 0;
-                }
-                __syncwarp();
-                const unsigned long long a2top = pre[128 + (M - 2)];
-                for (int q0 = lane; q0 < npv; q0 += 32 * kU) {
-                    unsigned long long tgk[kU];
-                    double vk[kU];
-                    unsigned bk[kU], pk[kU];
-                    bool ok[kU];
+                pair_prefix(occ, M, io, jo, bt, ks, pre);
+                for (int q0 = 0; q0 < npv; q0 += 32 * kU) {
+                    SFCI_CLEAR();
 #pragma unroll
                     for (int k = 0; k < kU; ++k) {
-                        const int q = q0 + 32 * k;
-                        ok[k] = false;
+                        const int q = q0 + 32 * k + lane;
                         if (q >= npv) continue;
                         const int a = vir[pv[2 * q]], b = vir[pv[2 * q + 1]];
-                        const int q1 = __popcll(rem & ((1ull << a) - 1ull));
-                        const int q2 = __popcll(rem & ((1ull << b) - 1ull));
-                        const unsigned long long h2 = pre[q1] + bt[a * ks + q1 + 1] + pre[64 + q2] -
-                                                      pre[64 + q1] + bt[b * ks + q2 + 2] + a2top -
-                                                      pre[128 + q2];
-                        const unsigned long long tg = spin ? hA * cb + h2 : h2 * cb + hB;
-                        if (!wanted<kMode>(o, tg)) continue;
+                        const unsigned long long h2 = pair_rank(rem, a, b, M, pre, bt, ks);
+                        const unsigned long long ta = spin ? hA : h2, tb = spin ? h2 : hB;
+                        if (!wanted<kMode>(o, ta, tb)) continue;
                         const int s1 = parity64(str & between_mask(i, a));
                         const unsigned long long s1s = str ^ (1ull << i) ^ (1ull << a);
                         const int s2 = parity64(s1s & between_mask(j, b));
-                        const double e = flip(__dsub_rn(__ldg(&g[(size_t(a * n + i) * n + b) * n + j]),
-                                                        __ldg(&g[(size_t(a * n + j) * n + b) * n + i])),
-                                              unsigned(s1 ^ s2));
-                        if (kMode != kModeBucket) {
-                            deliver<kMode>(o, off + (long long)p * npv + q, s, tg, e, c, inserted);
-                            continue;
-                        }
-                        vk[k] = __dmul_rn(e, c);
-                        tgk[k] = tg;
-                        bk[k] = bucket_of(tg, o.b.log2B);
-                        ok[k] = nonzero(vk[k]);
+                        want[k] = true, ha[k] = ta, hb[k] = tb, di[k] = off + (long long)p * npv + q;
+                        e[k] = flip(__dsub_rn(__ldg(&g[(size_t(a * n + i) * n + b) * n + j]),
+                                              __ldg(&g[(size_t(a * n + j) * n + b) * n + i])),
+                                    unsigned(s1 ^ s2));
                     }
-                    if (kMode == kModeBucket) {
-#pragma unroll
-                        for (int k = 0; k < kU; ++k)
-                            if (ok[k]) pk[k] = atomicAdd(&o.b.count[bk[k]], 1u);
-#pragma unroll
-                        for (int k = 0; k < kU; ++k)
-                            if (ok[k]) bucket_store(o.b, bk[k], pk[k], tgk[k], vk[k]);
-                    }
+                    emit_round<kMode>(o, want, ha, hb, e, di, s, c, cb, inserted);
                 }
                 __syncwarp();
             }
             off += (long long)npo * npv;
         }
-        // opposite-spin doubles: alpha hop x, beta hop y
+        // opposite-spin doubles: alpha hop x (row rankA1[x]), beta hops y
         for (int x = 0; x < d.sa; ++x) {
-            const unsigned long long ra = rankA1[x] * cb;
+            const unsigned long long ra = rankA1[x];
+            if (kMode == kModeBucket && !row_in_pass(o.b, ra)) continue;
             const unsigned oa = offA1[x];
             const double *gx = g + (oa & 0x7fffffffu);
             const unsigned sa = oa >> 31;
-            for (int y0 = lane; y0 < d.sb; y0 += 32 * kU) {
-                unsigned long long tgk[kU];
-                double vk[kU];
-                unsigned bk[kU], pk[kU];
-                bool ok[kU];
+            for (int y0 = 0; y0 < d.sb; y0 += 32 * kU) {
+                SFCI_CLEAR();
 #pragma unroll
                 for (int k = 0; k < kU; ++k) {
-                    const int y = y0 + 32 * k;
-                    ok[k] = false;
-                    if (y >= d.sb) continue;
-                    const unsigned long long tg = ra + rankB1[y];
-                    if (!wanted<kMode>(o, tg)) continue;
+                    const int y = y0 + 32 * k + lane;
+                    if (y >= d.sb || !wanted<kMode>(o, ra, rankB1[y])) continue;
                     const unsigned ob = offB1[y];
-                    const double e = flip(__ldg(&gx[ob & 0x7fffffffu]), sa ^ (ob >> 31));
-                    if (kMode != kModeBucket) {
-                        deliver<kMode>(o, off + (long long)x * d.sb + y, s, tg, e, c, inserted);
-                        continue;
-                    }
-                    vk[k] = __dmul_rn(e, c);
-                    tgk[k] = tg;
-                    bk[k] = bucket_of(tg, o.b.log2B);
-                    ok[k] = nonzero(vk[k]);
+                    want[k] = true, ha[k] = ra, hb[k] = rankB1[y], di[k] = off + (long long)x * d.sb + y;
+                    e[k] = flip(__ldg(&gx[ob & 0x7fffffffu]), sa ^ (ob >> 31));
                 }
-                if (kMode == kModeBucket) {
-#pragma unroll
-                    for (int k = 0; k < kU; ++k)
-                        if (ok[k]) pk[k] = atomicAdd(&o.b.count[bk[k]], 1u);
-#pragma unroll
-                    for (int k = 0; k < kU; ++k)
-                        if (ok[k]) bucket_store(o.b, bk[k], pk[k], tgk[k], vk[k]);
-                }
+                emit_round<kMode>(o, want, ha, hb, e, di, s, c, cb, inserted);
             }
         }
+#undef SFCI_CLEAR
         __syncwarp();
     }
     if (kMode == kModeTable) {
         for (int w = 16; w > 0; w >>= 1) inserted += __shfl_xor_sync(kFull, inserted, w);
         if (lane == 0 && inserted) atomicAdd(o.t.count, (unsigned long long)inserted);
+    }
+}
+
+// weights[ha] += elements bound for row ha: the source's own row gets the
+// diagonal, its beta singles and beta-beta doubles; each alpha single's row
+// gets the single plus one element per beta hop; each alpha-alpha double's row
+// gets one element.  One warp per input determinant.
+__global__ void __launch_bounds__(kEmitThreads)
+row_weight_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank, long long n_in,
+                  unsigned long long *__restrict__ weights) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int n = d.n, ks = d.ks;
+    unsigned long long *bt = reinterpret_cast<unsigned long long *>(sm);
+    unsigned char *pairs = sm + align16(size_t(n + 1) * ks * 8);
+    for (int i = threadIdx.x; i < (n + 1) * ks; i += blockDim.x) bt[i] = d.binom[i];
+    for (int i = threadIdx.x; i < 2 * d.n_pairs; i += blockDim.x) pairs[i] = d.pairs[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *wb = sm + block_smem(d) + size_t(warp) * warp_smem(d);
+    unsigned long long *pre = reinterpret_cast<unsigned long long *>(wb);
+    unsigned char *occA = reinterpret_cast<unsigned char *>(pre + 192);
+    unsigned char *virA = occA + 64, *occB = occA + 128, *virB = occA + 192;
+    const unsigned char *pOA = pairs + 2 * d.pair_off[0], *pVA = pairs + 2 * d.pair_off[1];
+    const unsigned long long cb = d.cb;
+    const unsigned long long w_self = 1ull + d.sb + (unsigned long long)d.po_b * d.pv_b;
+    const unsigned long long w_single = 1ull + d.sb;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long s = gw; s < n_in; s += nw) {
+        const unsigned long long r = in_rank[s];
+        const unsigned long long hA = r / cb;
+        const unsigned long long alpha = string_unrank_warp(hA, n, d.na, bt, ks);
+        build_lists(alpha, 0ull, n, occA, virA, occB, virB);
+        __syncwarp();
+        if (lane == 0) atomicAdd(&weights[hA], w_self);
+        for (int x = lane; x < d.sa; x += 32) {
+            const int io = x / d.va, iv = x - io * d.va;
+            atomicAdd(&weights[string_rank(alpha ^ (1ull << occA[io]) ^ (1ull << virA[iv]), bt, ks)], w_single);
+        }
+        for (int p = 0; p < d.po_a; ++p) {
+            const int io = pOA[2 * p], jo = pOA[2 * p + 1];
+            const unsigned long long rem = alpha ^ (1ull << occA[io]) ^ (1ull << occA[jo]);
+            pair_prefix(occA, d.na, io, jo, bt, ks, pre);
+            for (int q = lane; q < d.pv_a; q += 32)
+                atomicAdd(&weights[pair_rank(rem, virA[pVA[2 * q]], virA[pVA[2 * q + 1]], d.na, pre, bt, ks)], 1ull);
+            __syncwarp();
+        }
     }
 }
 
@@ -453,6 +560,24 @@ cudaError_t launch_emit_buckets(const SysDev &d, const unsigned long long *in_ra
     EmitOut o{};
     o.b = b;
     return launch_emit_impl<kModeBucket>(d, in_rank, in_coef, n_in, o, st);
+}
+
+cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_rank, long long n_in,
+                               unsigned long long *weights, cudaStream_t st) {
+    if (n_in <= 0) return cudaSuccess;
+    const size_t smem = emit_smem_bytes(d, kEmitWarps);
+    cudaError_t e = cudaFuncSetAttribute(row_weight_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, row_weight_kernel, kEmitThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long want = (n_in + kEmitWarps - 1) / kEmitWarps;
+    long long grid = (long long)device_sms() * per_sm;
+    if (want < grid) grid = want;
+    count_launch();
+    row_weight_kernel<<<(unsigned)grid, kEmitThreads, smem, st>>>(d, in_rank, n_in, weights);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_debug_excitations(const SysDev &d, const unsigned long long *in_rank,

@@ -198,18 +198,30 @@ __device__ __forceinline__ long long table_find(const Table &t, unsigned long lo
 // Where the emit kernel sends each intermediate element.
 enum EmitMode { kModeTable = 0, kModeDebug = 1, kModeBucket = 2 };
 
-// Bucketed merge: an element of rank k goes to bucket mix(k) >> (64 - log2B);
-// this pass keeps buckets [lo, hi).  Bucket b's elements fill
-// elem[(b - lo) * cap ...] up to cap; the rest go to an overflow list.
+// How the intermediate elements are spread over merge buckets.  Row mode
+// (rowmap set): the elements of one target alpha string ("row") go to that
+// row's bucket; light rows share a bucket, a heavy row owns several and picks
+// one by a hash of the beta index.  The emit then writes each group of
+// elements bound for one row (e.g. the beta hops of one alpha hop) as one run.
+// Hash mode (no rowmap, for spaces with too many alpha strings to map):
+// bucket = mix64(rank) >> (64 - log2B).  Bucket b owns elements
+// [boff[b], boff[b+1]) of the element buffer.
+struct Buckets {
+    int log2B;
+    const unsigned long long *rowmap;  // [C(n, n_alpha)]: first bucket << 32 | count (0: none)
+    unsigned long long cb;             // C(n, n_beta)
+    const unsigned long long *boff;    // [B + 1]
+};
+
 struct BucketOut {
-    unsigned *count;          // [B] elements that arrived per bucket (all passes share it)
-    Slot *elem;               // [(hi - lo) * cap]
+    Buckets bk;
+    unsigned *count;          // [B] elements that arrived per bucket
+    Slot *elem;               // regions of buckets [lo, hi), relative to boff[lo]
     Slot *ovf;                // [ovf_cap]
     unsigned long long *ovf_n;
     long long ovf_cap;
-    int log2B;
-    unsigned lo, hi, cap;
-    int *status;              // bit 1: overflow list full
+    unsigned lo, hi;
+    int *status;              // bit 1: overflow list full; bit 4: an element had no bucket
 };
 
 struct EmitOut {
@@ -224,8 +236,25 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long key) {
     return key * 0x9E3779B97F4A7C15ull;
 }
 
-__device__ __forceinline__ unsigned bucket_of(unsigned long long key, int log2B) {
-    return log2B > 0 ? (unsigned)(mix64(key) >> (64 - log2B)) : 0u;
+constexpr unsigned kNoBucket = 0xffffffffu;
+
+// bucket of the determinant (alpha index ha, beta index hb)
+__device__ __forceinline__ unsigned bucket_ab(const Buckets &bk, unsigned long long ha,
+                                              unsigned long long hb) {
+    if (!bk.rowmap) {
+        const unsigned long long key = ha * bk.cb + hb;
+        return bk.log2B > 0 ? (unsigned)(mix64(key) >> (64 - bk.log2B)) : 0u;
+    }
+    const unsigned long long m = __ldg(&bk.rowmap[ha]);
+    const unsigned ns = (unsigned)m, first = (unsigned)(m >> 32);
+    if (ns <= 1) return ns ? first : kNoBucket;
+    return first + (unsigned)(((mix64(hb) >> 32) * ns) >> 32);
+}
+
+__device__ __forceinline__ unsigned bucket_key(const Buckets &bk, unsigned long long key) {
+    if (!bk.rowmap) return bk.log2B > 0 ? (unsigned)(mix64(key) >> (64 - bk.log2B)) : 0u;
+    const unsigned long long ha = key / bk.cb;
+    return bucket_ab(bk, ha, key - ha * bk.cb);
 }
 
 // ------------------------------------------------------------- launchers
@@ -238,6 +267,10 @@ cudaError_t launch_emit(const SysDev &d, const unsigned long long *in_rank,
 cudaError_t launch_emit_buckets(const SysDev &d, const unsigned long long *in_rank,
                                 const double *in_coef, long long n_in, const BucketOut &b,
                                 cudaStream_t st);
+// weights[ha] += intermediate elements bound for alpha string ha (enumerated,
+// zeros included), over all input determinants
+cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_rank, long long n_in,
+                               unsigned long long *weights, cudaStream_t st);
 cudaError_t launch_debug_excitations(const SysDev &d, const unsigned long long *in_rank,
                                      long long n_in, long long *src, unsigned long long *tgt,
                                      double *elem, cudaStream_t st);
@@ -286,10 +319,10 @@ struct SigPack {
     double *p[kMaxVec];
 };
 struct MergeArgs {
-    unsigned lo, hi, cap;
-    int log2B;
+    unsigned lo, hi;
+    Buckets bk;
     const unsigned *count;              // [B] elements per bucket
-    const Slot *elem;                   // pass buckets' regions, cap each
+    const Slot *elem;                   // regions of the pass buckets, relative to boff[lo]
     const Slot *ovf_sorted;             // overflow elements sorted by bucket
     const unsigned long long *ovf_off;  // [hi - lo + 1]
     long long ovf_cap;                  // entries of ovf_sorted
@@ -302,27 +335,36 @@ struct MergeArgs {
     double *out_val;
     long long out_cap;
     unsigned long long *out_n;
-    unsigned long long *hist;           // [4096] top-12-bit histogram of |streamed values|
-    double *sumsq;
+    double tau;                         // stream out only |u| >= tau (0: every non-zero entry)
+    double *sumsq;                      // sum of u^2 over the non-zero entries off w_i, w_{i-1}
     unsigned long long *n_live;         // entries that survive the screen
+    unsigned long long *n_nonzero;      // non-zero entries off w_i, w_{i-1} (streamed or not)
     unsigned *queue;
     int *status;                        // bit 2: a bucket has too many distinct keys; bit 3: output full
 };
 size_t scan_ws_bytes(long long m);
 cudaError_t exclusive_scan(const unsigned *in, long long m, unsigned long long *out, void *ws,
                            cudaStream_t st);
-cudaError_t sort_overflow(const unsigned *count, unsigned lo, unsigned nb, unsigned cap,
+cudaError_t sort_overflow(const Buckets &bk, const unsigned *count, unsigned lo, unsigned nb,
                           const Slot *ovf, const unsigned long long *ovf_n, long long ovf_cap,
-                          int log2B, unsigned *tmp_counts, unsigned long long *off, void *scan_ws,
-                          Slot *out, cudaStream_t st);
-cudaError_t sort_probes(const VecRef *vecs, int nvec, int log2B, unsigned *pcount,
-                        unsigned long long *poff, void *scan_ws, Probe *out, cudaStream_t st);
+                          unsigned *tmp_counts, unsigned long long *off, void *scan_ws, Slot *out,
+                          cudaStream_t st);
+// probes of rows that receive no element get sigma = 0 written at once
+cudaError_t sort_probes(const Buckets &bk, unsigned long long nbuckets, const VecRef *vecs,
+                        double *const *sigw, int nvec, unsigned *pcount, unsigned long long *poff,
+                        void *scan_ws, Probe *out, cudaStream_t st);
+// boff[b] = b * cap for the hash mode's uniform regions
+cudaError_t uniform_offsets(unsigned long long *boff, unsigned long long nb, unsigned cap,
+                            cudaStream_t st);
 // slots: shared-memory table size (2048, 4096 or 8192 keys)
 cudaError_t launch_merge(const MergeArgs &A, int slots, cudaStream_t st);
 cudaError_t launch_u_entries(VecRef wi, const double *sig_i, VecRef wm, const double *sig_m,
                              double a, double b, unsigned long long *out_key, double *out_val,
-                             unsigned long long base_n, long long out_cap, unsigned long long *hist,
-                             double *sumsq, int *status, cudaStream_t st);
+                             unsigned long long base_n, long long out_cap, double *sumsq,
+                             int *status, cudaStream_t st);
+// *out = min |val[k]| over the first *n_dev entries (+inf when none)
+cudaError_t min_abs(const double *val, const unsigned long long *n_dev, long long cap, double *out,
+                    cudaStream_t st);
 size_t aligned_dots_ws_bytes(int nvec);
 cudaError_t aligned_dots(const VecRef *vecs, double *const *sig, int nvec, double *out_dev, void *ws,
                          cudaStream_t st);
@@ -343,16 +385,16 @@ struct Items {
 cudaError_t select_topk(Items it, long long k, unsigned long long *out_key, double *out_val,
                         unsigned long long *n_out_dev, double *sumsq_dev,
                         unsigned long long *total_dev, void *ws, size_t ws_bytes, cudaStream_t st);
-// Two-level top-k over items whose first-digit histogram (top 12 bits of the
-// composite key, 4096 bins) is already known: pick the bin, then one pass
-// writes every item of a smaller bin to out and every item of the picked bin
-// to cand.  *state_host receives {n_out, n_cand, need, all, done}; the caller
+// Two-level top-k: one pass histograms the first digit (top 12 bits of the
+// composite key, 4096 bins), the bin holding the k-th item is picked, and one
+// more pass writes every item of a smaller bin to out and every item of the
+// picked bin to cand.  *state_host receives {n_out, n_cand, need, all, done}; the caller
 // finishes with select_topk over the candidates when !done.
 struct SplitResult {
     unsigned long long n_out, n_cand, need, total;
     int all, done;
 };
-cudaError_t select_split(Items it, long long k, const unsigned long long *hist0,
+cudaError_t select_split(Items it, long long k,
                          unsigned long long *out_key, double *out_val, unsigned long long *n_out_dev,
                          unsigned long long *cand_key, double *cand_val, long long cand_cap,
                          unsigned long long *cand_n, void *ws, size_t ws_bytes, SplitResult *res_host,

@@ -14,6 +14,7 @@
 //   compares successive lambda_min.
 // The host sees only O(N_L) scalars per step.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -174,7 +175,8 @@ struct sfci_lanczos {
         size_t bytes = 0;
     };
     Buf bcount, belem, bovf, bovf_sorted, tmp_counts, ovf_off, probes, pcount, poff, scan_ws,
-        sig_key, sig_val, cand_key, cand_val;
+        sig_key, sig_val, cand_key, cand_val, weights, rowmap, boff;
+    std::vector<unsigned long long> h_weights, h_map, h_boff;
     long long sig_cap = 0, ovf_cap = 0, cand_cap = 0;
     double *sigw[kMaxVec] = {};
     char *words = nullptr;  // hist[4096] | outn | mlive | ovf_n | cand_n | msumsq | queue | mstatus
@@ -183,8 +185,12 @@ struct sfci_lanczos {
     double *msumsq = nullptr;
     unsigned *queue = nullptr;
     int *mstatus = nullptr;
-    int log2B_last = 0;
-    double ms_emit = 0, ms_merge = 0;
+    double ms_emit = 0, ms_merge = 0, ms_plan = 0, budget_gb = 0;
+    double tau_prev = 0.0;             // previous truncation cut in u (0: none)
+    unsigned long long stream_prev = 0;  // entries streamed by the previous merge
+    unsigned long long *nnz = nullptr;  // device word: non-zero entries off w_i, w_{i-1}
+    double *dmin = nullptr;             // device word: min |kept|
+    int n_passes = 0, nb_log2 = 0;
 };
 
 namespace {
@@ -197,7 +203,7 @@ void destroy_lz(sfci_lanczos *z) {
     cudaFree(z->scratch);
     for (auto *b : {&z->bcount, &z->belem, &z->bovf, &z->bovf_sorted, &z->tmp_counts, &z->ovf_off,
                     &z->probes, &z->pcount, &z->poff, &z->scan_ws, &z->sig_key, &z->sig_val,
-                    &z->cand_key, &z->cand_val})
+                    &z->cand_key, &z->cand_val, &z->weights, &z->rowmap, &z->boff})
         cudaFree(b->p);
     cudaFree(z->words);
     for (int j = 0; j < kMaxVec; ++j) cudaFree(z->sigw[j]);
@@ -255,13 +261,22 @@ sfci_status table_topk(sfci_lanczos *z, unsigned long long cap, int dst, double 
     return SFCI_OK;
 }
 
-// make buffer b hold at least `want` bytes (contents are not kept)
-sfci_status ensure(sfci_lanczos::Buf &b, size_t want, cudaStream_t st, const char *what) {
+// make buffer b hold at least `want` bytes (contents are not kept); a buffer
+// that has to grow gets `headroom` more, so a slowly growing need does not
+// re-allocate every step
+sfci_status ensure(sfci_lanczos::Buf &b, size_t want, cudaStream_t st, const char *what,
+                   double headroom = 1.0) {
     if (b.p && b.bytes >= want) return SFCI_OK;
     SFCI_CUDA(cudaStreamSynchronize(st));
     cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
+    if (headroom > 1.0) {
+        size_t free_b = 0, tot_b = 0;
+        cudaMemGetInfo(&free_b, &tot_b);
+        const size_t grown = size_t((double)want * headroom);
+        if (grown < free_b / 10 * 9) want = grown;
+    }
     cudaError_t e = cudaMalloc(&b.p, want > 0 ? want : 16);
     if (e != cudaSuccess) {
         set_error(std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
@@ -276,23 +291,95 @@ T *P(const sfci_lanczos::Buf &b) {
     return static_cast<T *>(b.p);
 }
 
+// Row mode is used when the alpha strings can be mapped densely.
+constexpr unsigned long long kMaxRows = 1ull << 26;
+
 // sigma_i = H w_i through the bucketed merge, with the probes of w_0..w_i.
 // On return the streamed entries sit in sig_key/sig_val[0, *n_out) and sigma at
 // every basis entry in sigw[j].
-sfci_status bucketed_sigma(sfci_lanczos *z, int i, unsigned long long *n_out, unsigned long long *n_live,
-                           double *sumsq) {
+sfci_status bucketed_sigma(sfci_lanczos *z, int i, double tau, unsigned long long *n_out,
+                           unsigned long long *n_live, unsigned long long *n_nonzero, double *sumsq) {
     const SysDev &d = z->sys->d;
     const long long n_in = z->wn[i];
     const double E = (double)n_in * (double)(d.n_conn + 1);
-    // buckets of ~bucket_elems elements; the merge table holds twice that many keys
-    const double per_bucket = z->p.bucket_elems > 0 ? (double)z->p.bucket_elems : 2048.0;
+    const double per_bucket = z->p.bucket_elems > 0 ? (double)z->p.bucket_elems : 1024.0;
     const int slots = per_bucket <= 1024.0 ? 2048 : (per_bucket <= 2048.0 ? 4096 : 8192);
-    int log2B = 4;
-    while (log2B < 28 && (double)(1ull << log2B) * per_bucket < E) ++log2B;
-    if (z->log2B_last > log2B) log2B = z->log2B_last;  // raised after a too-full bucket
-    // streamed-output capacity from the previous step (or the element count)
+    const bool row_mode = d.ca <= kMaxRows;
+    const auto t_plan0 = std::chrono::steady_clock::now();
+    sfci_status r;
+    Buckets bk{};
+    bk.cb = d.cb;
+    unsigned long long B = 0;
+    unsigned hash_cap = 0;
+    if (row_mode) {
+        // exact element count per target alpha string, then light rows packed
+        // into buckets of ~per_bucket elements and heavy rows split
+        const unsigned long long nrows = d.ca;
+        if ((r = ensure(z->weights, nrows * 8, z->st, "row weights", 1.5))) return r;
+        if ((r = ensure(z->rowmap, nrows * 8, z->st, "row map", 1.5))) return r;
+        SFCI_CUDA(cudaMemsetAsync(z->weights.p, 0, nrows * 8, z->st));
+        SFCI_CUDA(launch_row_weights(d, z->wr[i], n_in, static_cast<unsigned long long *>(z->weights.p), z->st));
+        z->h_weights.resize(nrows);
+        SFCI_CUDA(cudaMemcpyAsync(z->h_weights.data(), z->weights.p, nrows * 8, cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaStreamSynchronize(z->st));
+        z->h_map.assign(nrows, 0ull);
+        std::vector<unsigned long long> caps;
+        caps.reserve(size_t(E / per_bucket) + 16);
+        bool open = false;
+        double acc = 0.0;
+        for (unsigned long long row = 0; row < nrows; ++row) {
+            const unsigned long long w = z->h_weights[row];
+            if (!w) continue;
+            if ((double)w > per_bucket) {
+                const unsigned long long ns = (unsigned long long)std::ceil((double)w / per_bucket);
+                const unsigned long long per = (unsigned long long)std::ceil(1.2 * (double)w / (double)ns) + 64;
+                z->h_map[row] = ((unsigned long long)caps.size() << 32) | ns;
+                caps.insert(caps.end(), ns, per);
+                open = false;
+                continue;
+            }
+            if (!open || acc + (double)w > per_bucket) {
+                caps.push_back(0);
+                acc = 0.0;
+                open = true;
+            }
+            caps.back() += w;
+            acc += (double)w;
+            z->h_map[row] = ((unsigned long long)(caps.size() - 1) << 32) | 1ull;
+        }
+        B = caps.size();
+        if (B >= (1ull << 31)) {
+            set_error("too many merge buckets");
+            return SFCI_E_CAPACITY;
+        }
+        z->h_boff.resize(B + 1);
+        z->h_boff[0] = 0;
+        for (unsigned long long b = 0; b < B; ++b) z->h_boff[b + 1] = z->h_boff[b] + caps[b];
+        if ((r = ensure(z->boff, (B + 1) * 8, z->st, "bucket offsets", 1.5))) return r;
+        SFCI_CUDA(cudaMemcpyAsync(z->rowmap.p, z->h_map.data(), nrows * 8, cudaMemcpyHostToDevice, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(z->boff.p, z->h_boff.data(), (B + 1) * 8, cudaMemcpyHostToDevice, z->st));
+        bk.rowmap = static_cast<const unsigned long long *>(z->rowmap.p);
+        bk.log2B = 0;
+    } else {
+        int log2B = 4;
+        while (log2B < 30 && (double)(1ull << log2B) * per_bucket < E) ++log2B;
+        B = 1ull << log2B;
+        hash_cap = (unsigned)(std::ceil(1.125 * E / (double)B) + 128.0) & ~7u;
+        if ((r = ensure(z->boff, (B + 1) * 8, z->st, "bucket offsets", 1.5))) return r;
+        SFCI_CUDA(uniform_offsets(static_cast<unsigned long long *>(z->boff.p), B, hash_cap, z->st));
+        z->h_boff.resize(B + 1);
+        for (unsigned long long b = 0; b <= B; ++b) z->h_boff[b] = b * hash_cap;
+        bk.log2B = log2B;
+    }
+    bk.boff = static_cast<const unsigned long long *>(z->boff.p);
+    const unsigned long long total_cap = z->h_boff[B];
+
+    // streamed-output capacity: with a threshold, a few N_d (from the previous
+    // merge); without, all of sigma (from the previous step or the element count)
     double sig_need;
-    if (z->m_prev > 0 && z->nin_prev > 0)
+    if (tau > 0.0)
+        sig_need = std::max(16.0 * (double)z->nkeep, 1.5 * (double)z->stream_prev);
+    else if (z->m_prev > 0 && z->nin_prev > 0)
         sig_need = 1.3 * (double)z->m_prev * std::max(1.0, (double)n_in / (double)z->nin_prev);
     else
         sig_need = E;
@@ -301,80 +388,93 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, unsigned long long *n_out, un
     long long totp = 0;
     for (int j = 0; j <= i; ++j) totp += z->wn[j];
     for (int attempt = 0; attempt < 8; ++attempt) {
-        const unsigned long long B = 1ull << log2B;
         size_t free_b = 0, tot_b = 0;
         SFCI_CUDA(cudaMemGetInfo(&free_b, &tot_b));
         // memory the element regions may use: what is free plus what the big buffers hold
         const double held = (double)z->belem.bytes + (double)z->sig_key.bytes + (double)z->sig_val.bytes;
-        const double budget = 0.85 * ((double)free_b + held) - sig_need * 16.0 - 2.0 * ovf_cap * 16.0;
-        const unsigned cap = (unsigned)(std::ceil(1.125 * E / (double)B) + 128.0) & ~7u;
-        if (budget <= (double)cap * sizeof(Slot)) {
-            set_error("not enough device memory for sigma");
-            return SFCI_E_CAPACITY;
+        const double budget = 0.85 * ((double)free_b + held) - 1.1 * sig_need * 16.0 - 2.0 * ovf_cap * 16.0;
+        // passes: contiguous bucket ranges whose regions fit the budget
+        std::vector<unsigned long long> cuts{0};
+        unsigned long long max_pass = 0;
+        for (unsigned long long b = 0; b < B;) {
+            unsigned long long hi = b + 1;
+            while (hi < B && (double)(z->h_boff[hi + 1] - z->h_boff[b]) * sizeof(Slot) <= budget) ++hi;
+            if ((double)(z->h_boff[hi] - z->h_boff[b]) * sizeof(Slot) > budget) {
+                set_error("not enough device memory for one merge bucket");
+                return SFCI_E_CAPACITY;
+            }
+            max_pass = std::max(max_pass, z->h_boff[hi] - z->h_boff[b]);
+            cuts.push_back(hi);
+            b = hi;
         }
-        int npass = 1;
-        while ((double)((B + npass - 1) / npass) * cap * sizeof(Slot) > budget && npass < 4096) ++npass;
-        const unsigned long long Bp = (B + npass - 1) / npass;
-        const long long scap = (long long)sig_need;
-        sfci_status r;
-        const size_t want_elem = size_t(Bp) * cap * sizeof(Slot), want_sig = size_t(scap) * 8;
+        const int npass = (int)cuts.size() - 1;
+        const size_t want_elem = size_t(max_pass) * sizeof(Slot);
+        size_t want_sig = size_t(sig_need) * 8;
         if (z->belem.bytes < want_elem || z->sig_key.bytes < want_sig || z->sig_val.bytes < want_sig) {
-            // the three large buffers are sized together from one budget: free them all first
+            // the three large buffers are sized together from one budget: free them
+            // all, then give the sigma output 10 % headroom out of the same budget
             SFCI_CUDA(cudaStreamSynchronize(z->st));
             for (auto *bb : {&z->belem, &z->sig_key, &z->sig_val}) {
                 cudaFree(bb->p);
                 bb->p = nullptr;
                 bb->bytes = 0;
             }
+            want_sig = size_t(1.1 * sig_need) * 8;
         }
         if ((r = ensure(z->sig_key, want_sig, z->st, "sigma keys"))) return r;
         if ((r = ensure(z->sig_val, want_sig, z->st, "sigma values"))) return r;
-        z->sig_cap = scap;
+        z->sig_cap = (long long)(std::min(z->sig_key.bytes, z->sig_val.bytes) / 8);
         if ((r = ensure(z->belem, want_elem, z->st, "element regions"))) return r;
-        if ((r = ensure(z->bcount, size_t(B) * 4, z->st, "bucket counters"))) return r;
+        if ((r = ensure(z->bcount, size_t(B) * 4, z->st, "bucket counters", 1.5))) return r;
         if ((r = ensure(z->probes, size_t(std::max<long long>(totp, 1)) * sizeof(Probe), z->st, "probes"))) return r;
-        if ((r = ensure(z->pcount, size_t(B) * 4, z->st, "probe counts"))) return r;
-        if ((r = ensure(z->poff, size_t(B + 1) * 8, z->st, "probe offsets"))) return r;
-        if ((r = ensure(z->tmp_counts, size_t(B + 1) * 4, z->st, "overflow counts"))) return r;
-        if ((r = ensure(z->ovf_off, size_t(B + 1) * 8, z->st, "overflow offsets"))) return r;
+        if ((r = ensure(z->pcount, size_t(B) * 4, z->st, "probe counts", 1.5))) return r;
+        if ((r = ensure(z->poff, size_t(B + 1) * 8, z->st, "probe offsets", 1.5))) return r;
+        if ((r = ensure(z->tmp_counts, size_t(B + 1) * 4, z->st, "overflow counts", 1.5))) return r;
+        if ((r = ensure(z->ovf_off, size_t(B + 1) * 8, z->st, "overflow offsets", 1.5))) return r;
         if ((r = ensure(z->bovf, size_t(ovf_cap) * sizeof(Slot), z->st, "overflow list"))) return r;
         if ((r = ensure(z->bovf_sorted, size_t(ovf_cap) * sizeof(Slot), z->st, "sorted overflow"))) return r;
         z->ovf_cap = ovf_cap;
-        if ((r = ensure(z->scan_ws, scan_ws_bytes((long long)B + 1), z->st, "scan workspace"))) return r;
+        if ((r = ensure(z->scan_ws, scan_ws_bytes((long long)B + 1), z->st, "scan workspace", 1.5))) return r;
         for (int j = 0; j <= i; ++j)
             if (!z->sigw[j]) SFCI_CUDA(cudaMalloc(&z->sigw[j], size_t(z->nkeep) * 8));
+        (void)total_cap;
+        (void)hash_cap;
 
         // probes of w_0..w_i, bucketed once for all passes
         std::vector<VecRef> vr(i + 1);
         for (int j = 0; j <= i; ++j) vr[j] = VecRef{z->wr[j], z->wc[j], z->wn[j]};
-        SFCI_CUDA(sort_probes(vr.data(), i + 1, log2B, P<unsigned>(z->pcount), P<unsigned long long>(z->poff),
-                              z->scan_ws.p, P<Probe>(z->probes), z->st));
+        SFCI_CUDA(sort_probes(bk, B, vr.data(), z->sigw, i + 1, P<unsigned>(z->pcount),
+                              P<unsigned long long>(z->poff), z->scan_ws.p, P<Probe>(z->probes), z->st));
         SFCI_CUDA(cudaMemsetAsync(z->bcount.p, 0, B * 4, z->st));
         SFCI_CUDA(cudaMemsetAsync(z->words, 0, 4096 * 8 + 1024, z->st));
+        SFCI_CUDA(cudaStreamSynchronize(z->st));
+        z->ms_plan = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan0).count();
+        z->budget_gb = budget / 1e9;
+        z->n_passes = npass;
+        z->nb_log2 = 0;
+        while ((1ull << z->nb_log2) < B) ++z->nb_log2;
         z->ms_emit = z->ms_merge = 0.0;
         for (int pass = 0; pass < npass; ++pass) {
-            const unsigned lo = (unsigned)(pass * Bp);
-            const unsigned hi = (unsigned)std::min<unsigned long long>(B, (pass + 1) * Bp);
-            if (lo >= hi) break;
+            const unsigned lo = (unsigned)cuts[pass], hi = (unsigned)cuts[pass + 1];
             SFCI_CUDA(cudaMemsetAsync(z->ovf_n, 0, 8, z->st));
             BucketOut bo;
+            bo.bk = bk;
             bo.count = P<unsigned>(z->bcount);
             bo.elem = P<Slot>(z->belem);
             bo.ovf = P<Slot>(z->bovf);
             bo.ovf_n = z->ovf_n;
             bo.ovf_cap = z->ovf_cap;
-            bo.log2B = log2B;
-            bo.lo = lo, bo.hi = hi, bo.cap = cap;
+            bo.lo = lo, bo.hi = hi;
             bo.status = z->mstatus;
             SFCI_CUDA(cudaEventRecord(z->evp[0], z->st));
             SFCI_CUDA(launch_emit_buckets(d, z->wr[i], z->wc[i], n_in, bo, z->st));
             SFCI_CUDA(cudaEventRecord(z->evp[1], z->st));
-            SFCI_CUDA(sort_overflow(P<unsigned>(z->bcount), lo, hi - lo, cap, P<Slot>(z->bovf), z->ovf_n,
-                                    z->ovf_cap, log2B, P<unsigned>(z->tmp_counts),
-                                    P<unsigned long long>(z->ovf_off), z->scan_ws.p, P<Slot>(z->bovf_sorted),
-                                    z->st));
+            SFCI_CUDA(sort_overflow(bk, P<unsigned>(z->bcount), lo, hi - lo, P<Slot>(z->bovf), z->ovf_n,
+                                    z->ovf_cap, P<unsigned>(z->tmp_counts), P<unsigned long long>(z->ovf_off),
+                                    z->scan_ws.p, P<Slot>(z->bovf_sorted), z->st));
             MergeArgs A{};
-            A.lo = lo, A.hi = hi, A.cap = cap, A.log2B = log2B;
+            A.lo = lo, A.hi = hi;
+            A.bk = bk;
             A.count = P<unsigned>(z->bcount);
             A.elem = P<Slot>(z->belem);
             A.ovf_sorted = P<Slot>(z->bovf_sorted);
@@ -390,9 +490,10 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, unsigned long long *n_out, un
             A.out_val = P<double>(z->sig_val);
             A.out_cap = z->sig_cap;
             A.out_n = z->outn;
-            A.hist = z->hist;
+            A.tau = tau;
             A.sumsq = z->msumsq;
             A.n_live = z->mlive;
+            A.n_nonzero = z->nnz;
             A.queue = z->queue;
             A.status = z->mstatus;
             SFCI_CUDA(launch_merge(A, slots, z->st));
@@ -404,21 +505,28 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, unsigned long long *n_out, un
             z->ms_emit += a, z->ms_merge += b;
         }
         int hs = 0;
-        unsigned long long ho = 0, hl = 0, hv = 0;
+        unsigned long long ho = 0, hl = 0, hz = 0;
         double hq = 0.0;
         SFCI_CUDA(cudaMemcpyAsync(&hs, z->mstatus, 4, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaMemcpyAsync(&ho, z->outn, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaMemcpyAsync(&hl, z->mlive, 8, cudaMemcpyDeviceToHost, z->st));
-        SFCI_CUDA(cudaMemcpyAsync(&hv, z->ovf_n, 8, cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(&hz, z->nnz, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaMemcpyAsync(&hq, z->msumsq, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaStreamSynchronize(z->st));
         if (hs == 0) {
-            z->log2B_last = 0;
-            *n_out = ho, *n_live = hl, *sumsq = hq;
+            *n_out = ho, *n_live = hl, *n_nonzero = hz, *sumsq = hq;
+            z->stream_prev = ho;
             return SFCI_OK;
         }
+        if (hs & 16) {
+            set_error("an intermediate element fell outside the row map");
+            return SFCI_E_INVALID;
+        }
+        if (hs & 4) {
+            set_error("a merge bucket held more distinct entries than its table");
+            return SFCI_E_CAPACITY;
+        }
         if (hs & 2) ovf_cap *= 4;
-        if (hs & 4) log2B += 1, z->log2B_last = log2B;
         if (hs & 8) sig_need = std::max(sig_need * 2.0, (double)ho * 1.3 + 2.0 * z->nkeep);
     }
     set_error("bucketed sigma did not fit after 8 attempts");
@@ -512,6 +620,8 @@ sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
         z->msumsq = reinterpret_cast<double *>(w + 32);
         z->queue = reinterpret_cast<unsigned *>(w + 40);
         z->mstatus = reinterpret_cast<int *>(w + 44);
+        z->nnz = reinterpret_cast<unsigned long long *>(w + 48);
+        z->dmin = reinterpret_cast<double *>(w + 56);
     }
     if (e != cudaSuccess) {
         destroy_lz(z);
@@ -554,54 +664,58 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
     const long long n_in = z->wn[i];
     SFCI_CUDA(cudaEventRecord(z->ev[0], z->st));
 
-    // ---- sigma_i = H w_i, bucketed merge with the probes of w_0..w_i
-    unsigned long long n_stream = 0, n_live = 0;
-    double sq = 0.0;
-    {
-        const sfci_status rs = bucketed_sigma(z, i, &n_stream, &n_live, &sq);
-        if (rs != SFCI_OK) return rs;
-    }
-    info->ms_sigma = z->ms_emit + z->ms_merge;
-    info->ms_emit = z->ms_emit;
-    info->ms_merge = z->ms_merge;
-    info->n_elements = n_in * (d.n_conn + 1);
-    z->m_prev = (long long)n_stream;
-    z->nin_prev = n_in;
-
-    // ---- T_ji = <w_j|sigma_i> from sigma recorded at w_j's entries, S_ji = <w_j|w_i>
+    bool last = (i == NL - 1) || (z->p.max_iter > 0 && z->iter + 1 >= z->p.max_iter);
+    // Stream threshold: a quarter of the previous cut; nothing at a cycle's last
+    // vector (u is not formed there); checked below, and redone with 0 if the
+    // N_d largest did not all clear it.
+    double tau = last ? __builtin_inf() : (z->tau_prev > 0.0 ? 0.25 * z->tau_prev : 0.0);
     std::vector<VecRef> vr(i + 1);
     for (int j = 0; j <= i; ++j) vr[j] = VecRef{z->wr[j], z->wc[j], z->wn[j]};
-    SFCI_CUDA(aligned_dots(vr.data(), z->sigw, i + 1, z->dT, z->scratch + z->off_dots, z->st));
-    SFCI_CUDA(vec_overlaps(vr.data(), i + 1, vr[i], z->dS, z->scratch + z->off_dots, z->st));
-    std::vector<double> tcol(i + 1), scol(i + 1);
-    SFCI_CUDA(cudaMemcpyAsync(tcol.data(), z->dT, 8 * (i + 1), cudaMemcpyDeviceToHost, z->st));
-    SFCI_CUDA(cudaMemcpyAsync(scol.data(), z->dS, 8 * (i + 1), cudaMemcpyDeviceToHost, z->st));
-    SFCI_CUDA(cudaStreamSynchronize(z->st));
-    for (int j = 0; j <= i; ++j) {
-        z->T[size_t(j) * NL + i] = tcol[j];
-        z->S[size_t(j) * NL + i] = scol[j];
-    }
-    z->iter += 1;
-    info->iter = z->iter;
-    info->cycle = z->cycle;
-    info->index = i;
-    info->n_in = n_in;
-    info->n_sigma = (long long)n_live;
-    const double a = tcol[i], b = i > 0 ? tcol[i - 1] : 0.0;
-    info->a = a;
-    info->b = b;
-    info->t00 = z->T[0];
+    for (int attempt = 0;; ++attempt) {
+        // ---- sigma_i = H w_i, bucketed merge with the probes of w_0..w_i
+        unsigned long long n_stream = 0, n_live = 0, n_nz = 0;
+        double sq = 0.0;
+        {
+            const sfci_status rs = bucketed_sigma(z, i, tau, &n_stream, &n_live, &n_nz, &sq);
+            if (rs != SFCI_OK) return rs;
+        }
+        info->ms_sigma = z->ms_emit + z->ms_merge;
+        info->ms_emit = z->ms_emit;
+        info->ms_merge = z->ms_merge;
+        info->ms_plan = z->ms_plan;
+        info->n_passes = z->n_passes;
+        info->n_buckets_log2 = z->nb_log2;
+        info->n_elements = n_in * (d.n_conn + 1);
+        info->n_sigma = (long long)n_live;
+        z->m_prev = (long long)n_live;
+        z->nin_prev = n_in;
 
-    bool last = (i == NL - 1) || (z->p.max_iter > 0 && z->iter >= z->p.max_iter);
-    if (!last) {
+        // ---- T_ji = <w_j|sigma_i> from sigma recorded at w_j's entries, S_ji = <w_j|w_i>
+        SFCI_CUDA(aligned_dots(vr.data(), z->sigw, i + 1, z->dT, z->scratch + z->off_dots, z->st));
+        SFCI_CUDA(vec_overlaps(vr.data(), i + 1, vr[i], z->dS, z->scratch + z->off_dots, z->st));
+        std::vector<double> tcol(i + 1), scol(i + 1);
+        SFCI_CUDA(cudaMemcpyAsync(tcol.data(), z->dT, 8 * (i + 1), cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(scol.data(), z->dS, 8 * (i + 1), cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaStreamSynchronize(z->st));
+        for (int j = 0; j <= i; ++j) {
+            z->T[size_t(j) * NL + i] = tcol[j];
+            z->S[size_t(j) * NL + i] = scol[j];
+        }
+        const double a = tcol[i], b = i > 0 ? tcol[i - 1] : 0.0;
+        info->a = a;
+        info->b = b;
+        info->t00 = z->T[0];
+        if (last) break;
+
         // u = sigma_i - a w_i - b w_{i-1} on the support of w_i and w_{i-1} (Eq. 10);
-        // elsewhere u = sigma_i, already streamed
+        // elsewhere u = sigma_i, streamed where |u| >= tau
+        SFCI_CUDA(cudaEventRecord(z->evp[3], z->st));
         const VecRef wi = vr[i];
         const VecRef wm = i > 0 ? vr[i - 1] : VecRef{nullptr, nullptr, 0};
         unsigned long long *skey = static_cast<unsigned long long *>(z->sig_key.p);
         double *sval = static_cast<double *>(z->sig_val.p);
         SFCI_CUDA(launch_u_entries(wi, z->sigw[i], wm, i > 0 ? z->sigw[i - 1] : nullptr, a, b, skey, sval,
-                                   n_stream, z->sig_cap, z->hist, z->msumsq, z->mstatus, z->st));
+                                   n_stream, z->sig_cap, z->msumsq, z->mstatus, z->st));
         const long long n_items = (long long)n_stream + wi.n + wm.n;
         // Eq. 11: top-N_d of u
         const long long cand_cap = std::max<long long>(4 * z->nkeep, 1 << 22);
@@ -611,7 +725,7 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
         z->cand_cap = cand_cap;
         Items it{skey, sval, 1, n_items};
         SplitResult res{};
-        SFCI_CUDA(select_split(it, z->nkeep, z->hist, z->wr[i + 1], z->wc[i + 1], z->ndev,
+        SFCI_CUDA(select_split(it, z->nkeep, z->wr[i + 1], z->wc[i + 1], z->ndev,
                                static_cast<unsigned long long *>(z->cand_key.p),
                                static_cast<double *>(z->cand_val.p), cand_cap, z->cand_n,
                                z->scratch + z->off_sel, z->sel_bytes, &res, z->st));
@@ -633,12 +747,11 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
             SFCI_CUDA(cudaStreamSynchronize(z->st));
             kept = std::min<unsigned long long>(kept + n2, (unsigned long long)z->nkeep);
         }
-        double usq = 0.0;
+        double usq = 0.0, cut = 0.0;
         int hs = 0;
         SFCI_CUDA(cudaMemcpyAsync(z->ndev, &kept, 8, cudaMemcpyHostToDevice, z->st));
-        SFCI_CUDA(sort_pairs(z->wr[i + 1], z->wc[i + 1], z->nkeep, z->ndev, key_bits(d.dim),
-                             z->scratch + z->off_sort, z->st));
-        SFCI_CUDA(normalize_vec(z->wc[i + 1], z->nkeep, z->ndev, z->scratch + z->off_norm, z->st));
+        SFCI_CUDA(min_abs(z->wc[i + 1], z->ndev, z->nkeep, z->dmin, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(&cut, z->dmin, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaMemcpyAsync(&usq, z->msumsq, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaMemcpyAsync(&hs, z->mstatus, 4, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaStreamSynchronize(z->st));
@@ -646,7 +759,29 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
             set_error("sigma output buffer overflowed while appending u");
             return SFCI_E_CAPACITY;
         }
+        // were all of the N_d largest streamed?  (entries below tau were not)
+        const bool complete = tau <= 0.0 || (kept == (unsigned long long)z->nkeep ? !(cut < tau)
+                                                                                  : n_nz + wi.n + wm.n <= (unsigned long long)n_items);
+        if (!complete) {
+            if (attempt > 0) {
+                set_error("truncation threshold check failed twice");
+                return SFCI_E_CAPACITY;
+            }
+            tau = 0.0;
+            continue;
+        }
+        z->tau_prev = kept == (unsigned long long)z->nkeep ? cut : 0.0;
+        SFCI_CUDA(sort_pairs(z->wr[i + 1], z->wc[i + 1], z->nkeep, z->ndev, key_bits(d.dim),
+                             z->scratch + z->off_sort, z->st));
+        SFCI_CUDA(normalize_vec(z->wc[i + 1], z->nkeep, z->ndev, z->scratch + z->off_norm, z->st));
         z->wn[i + 1] = (long long)kept;
+        SFCI_CUDA(cudaEventRecord(z->evp[0], z->st));
+        SFCI_CUDA(cudaEventSynchronize(z->evp[0]));
+        {
+            float tk = 0.f;
+            cudaEventElapsedTime(&tk, z->evp[3], z->evp[0]);
+            info->ms_topk = tk;
+        }
         const double unorm = std::sqrt(usq);
         info->u_norm = unorm;
         if (unorm < 1e-14 * std::fabs(a) || res.total == 0) {
@@ -656,7 +791,13 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
             info->n_kept = z->wn[i + 1];
             z->idx = i + 1;
         }
+        break;
     }
+    z->iter += 1;
+    info->iter = z->iter;
+    info->cycle = z->cycle;
+    info->index = i;
+    info->n_in = n_in;
     if (last) {
         const int m = i + 1;
         std::vector<double> Tm(size_t(m) * m), Sm(size_t(m) * m);

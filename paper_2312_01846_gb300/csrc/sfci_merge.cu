@@ -21,8 +21,10 @@
 // each probe up in shared memory and records sigma_k next to w_j's entry.  The
 // entries of w_i and w_{i-1} are left out of the streamed output; their
 // u = sigma - a w_i - b w_{i-1} values are formed later from the recorded
-// sigma_k (Eq. 10).  The streamed output and the u entries feed a top-k whose
-// first 12-bit histogram is accumulated by the merge itself.
+// sigma_k (Eq. 10).  Only entries with |u| >= tau are streamed out (tau below
+// the previous step's truncation cut; the caller checks afterwards that the
+// N_d largest all cleared it, and otherwise redoes the step with tau = 0), so
+// the truncation reads a few N_d entries instead of all of sigma.
 #include "sfci_internal.cuh"
 
 namespace sfci {
@@ -32,6 +34,8 @@ constexpr int kMT = 256;             // merge CTA threads
 constexpr int kPre = 8;              // elements each thread loads before inserting
 constexpr int kBins = 4096;
 
+// slot in the shared-memory table: hash bits below those that chose the
+// bucket (hash mode); row mode uses the top bits
 template <int kSlots>
 __device__ __forceinline__ unsigned smem_slot(unsigned long long key, int log2B) {
     return (unsigned)(mix64(key) >> (64 - log2B - 13)) & (kSlots - 1);
@@ -124,25 +128,26 @@ __global__ void scan_block_kernel(const unsigned *in, long long m, const unsigne
 
 // ------------------------------------------------------------- overflow
 
-// overflow elements per bucket of the pass = max(count - cap, 0)
-__global__ void ovf_counts_kernel(const unsigned *count, unsigned lo, unsigned nb, unsigned cap,
-                                  unsigned *ovc) {
+// overflow elements per bucket of the pass = max(count - capacity, 0)
+__global__ void ovf_counts_kernel(const unsigned long long *boff, const unsigned *count, unsigned lo,
+                                  unsigned nb, unsigned *ovc) {
     for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
          b += (long long)gridDim.x * blockDim.x) {
         const unsigned c = count[lo + b];
+        const unsigned cap = (unsigned)(boff[lo + b + 1] - boff[lo + b]);
         ovc[b] = c > cap ? c - cap : 0u;
     }
 }
 
-__global__ void ovf_scatter_kernel(const Slot *ovf, const unsigned long long *ovf_n, long long ovf_cap,
-                                   int log2B, unsigned lo, const unsigned long long *off,
+__global__ void ovf_scatter_kernel(Buckets bk, const Slot *ovf, const unsigned long long *ovf_n,
+                                   long long ovf_cap, unsigned lo, const unsigned long long *off,
                                    unsigned *fill, Slot *out) {
     long long n = (long long)*ovf_n;
     if (n > ovf_cap) n = ovf_cap;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const ulonglong2 e = reinterpret_cast<const ulonglong2 *>(ovf)[i];
-        const unsigned b = bucket_of(e.x, log2B) - lo;
+        const unsigned b = bucket_key(bk, e.x) - lo;
         const unsigned long long pos = off[b] + atomicAdd(&fill[b], 1u);
         // offsets count every overflowing element; a truncated list (status
         // bit 1, the sigma is redone) must not write past its end
@@ -152,23 +157,27 @@ __global__ void ovf_scatter_kernel(const Slot *ovf, const unsigned long long *ov
 
 // ------------------------------------------------------------- probes
 
-__global__ void probe_count_kernel(VecPackRef vp, int nvec, int log2B, unsigned *pcount) {
+__global__ void probe_count_kernel(Buckets bk, VecPackRef vp, SigPack sp, int nvec, unsigned *pcount) {
     for (int j = 0; j < nvec; ++j) {
         const VecRef w = vp.v[j];
         for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < w.n;
-             k += (long long)gridDim.x * blockDim.x)
-            atomicAdd(&pcount[bucket_of(w.rank[k], log2B)], 1u);
+             k += (long long)gridDim.x * blockDim.x) {
+            const unsigned b = bucket_key(bk, w.rank[k]);
+            if (b == kNoBucket) sp.p[j][k] = 0.0;  // no element reaches this row
+            else atomicAdd(&pcount[b], 1u);
+        }
     }
 }
 
-__global__ void probe_scatter_kernel(VecPackRef vp, int nvec, int log2B,
-                                     const unsigned long long *poff, unsigned *pfill, Probe *out) {
+__global__ void probe_scatter_kernel(Buckets bk, VecPackRef vp, int nvec, const unsigned long long *poff,
+                                     unsigned *pfill, Probe *out) {
     for (int j = 0; j < nvec; ++j) {
         const VecRef w = vp.v[j];
         for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < w.n;
              k += (long long)gridDim.x * blockDim.x) {
             const unsigned long long key = w.rank[k];
-            const unsigned b = bucket_of(key, log2B);
+            const unsigned b = bucket_key(bk, key);
+            if (b == kNoBucket) continue;
             const unsigned long long pos = poff[b] + atomicAdd(&pfill[b], 1u);
             Probe p;
             p.key = key;
@@ -176,6 +185,12 @@ __global__ void probe_scatter_kernel(VecPackRef vp, int nvec, int log2B,
             out[pos] = p;
         }
     }
+}
+
+__global__ void uniform_offsets_kernel(unsigned long long *boff, unsigned long long nb, unsigned cap) {
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; b <= nb;
+         b += (unsigned long long)gridDim.x * blockDim.x)
+        boff[b] = b * cap;
 }
 
 // ------------------------------------------------------------- merge
@@ -191,28 +206,28 @@ merge_kernel(MergeArgs A) {
     extern __shared__ __align__(16) unsigned char msm[];
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(msm);
     double *vals = reinterpret_cast<double *>(keys + kSlots);
-    unsigned *hist = reinterpret_cast<unsigned *>(vals + kSlots);
-    unsigned short *occ = reinterpret_cast<unsigned short *>(hist + kBins);
+    unsigned short *occ = reinterpret_cast<unsigned short *>(vals + kSlots);
     unsigned char *flag = reinterpret_cast<unsigned char *>(occ + kSlots);
     __shared__ unsigned cur, n_occ;
     const int tid = threadIdx.x, lane = tid & 31;
     const bool screen = A.eps > 0.0;
-    for (int b = tid; b < kBins; b += kMT) hist[b] = 0;
     for (int sl = tid; sl < kSlots; sl += kMT) keys[sl] = kEmpty, vals[sl] = 0.0, flag[sl] = 0;
     if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u);
     double sq = 0.0;
-    unsigned long long n_live = 0;
+    unsigned long long n_live = 0, n_nonzero = 0;
     __syncthreads();
     for (;;) {
         const unsigned bi = cur;  // bucket index within the pass
         if (bi >= A.hi - A.lo) break;
         const unsigned b = A.lo + bi;
         const unsigned cnt = A.count[b];
-        const unsigned n_main = cnt < A.cap ? cnt : A.cap;
+        const unsigned long long r0 = A.bk.boff[b];
+        const unsigned bcap = (unsigned)(A.bk.boff[b + 1] - r0);
+        const unsigned n_main = cnt < bcap ? cnt : bcap;
         unsigned long long o0 = A.ovf_off[bi], o1 = A.ovf_off[bi + 1];
         if (o1 > (unsigned long long)A.ovf_cap) o1 = (unsigned long long)A.ovf_cap;  // truncated list
         if (o0 > o1) o0 = o1;
-        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(A.elem) + size_t(bi) * A.cap;
+        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(A.elem) + (r0 - A.bk.boff[A.lo]);
         const ulonglong2 *ovs = reinterpret_cast<const ulonglong2 *>(A.ovf_sorted) + o0;
         const unsigned total = n_main + (unsigned)(o1 - o0);
         for (unsigned e0 = 0; e0 < total; e0 += kMT * kPre) {
@@ -227,7 +242,7 @@ merge_kernel(MergeArgs A) {
             for (int k = 0; k < kPre; ++k) {
                 const unsigned long long key = x[k].x;
                 if (key == kEmpty) continue;
-                unsigned h = smem_slot<kSlots>(key, A.log2B);
+                unsigned h = smem_slot<kSlots>(key, A.bk.rowmap ? 0 : A.bk.log2B);
                 int probe = 0;
                 for (; probe < kSlots; ++probe) {
                     const unsigned long long c = keys[h];
@@ -251,7 +266,7 @@ merge_kernel(MergeArgs A) {
         const unsigned long long p0 = A.probe_off[b], p1 = A.probe_off[b + 1];
         for (unsigned long long p = p0 + tid; p < p1; p += kMT) {
             const Probe pr = A.probes[p];
-            unsigned h = smem_slot<kSlots>(pr.key, A.log2B);
+            unsigned h = smem_slot<kSlots>(pr.key, A.bk.rowmap ? 0 : A.bk.log2B);
             int found = -1;
             for (int q = 0; q < kSlots; ++q) {
                 const unsigned long long c = keys[h];
@@ -270,8 +285,8 @@ merge_kernel(MergeArgs A) {
             if (found >= 0 && (j == A.ja || j == A.jb)) flag[found] = 1;
         }
         __syncthreads();
-        // stream the occupied slots out (u = sigma there), histogram of |u|,
-        // and clear them for the next bucket
+        // stream the occupied slots with |u| >= tau out (u = sigma there) and
+        // clear them for the next bucket
         const unsigned nocc = n_occ;
         for (unsigned t0 = 0; t0 < nocc; t0 += kMT) {
             const unsigned t = t0 + tid;
@@ -283,7 +298,12 @@ merge_kernel(MergeArgs A) {
                 key = keys[sl];
                 v = vals[sl];
                 live = !(screen && fabs(v) < A.eps);
-                w = live && !flag[sl];
+                const bool nz = live && !flag[sl] && (((unsigned long long)__double_as_longlong(v) << 1) != 0ull);
+                if (nz) {
+                    ++n_nonzero;
+                    sq = __fma_rn(v, v, sq);
+                }
+                w = nz && !(fabs(v) < A.tau);
                 keys[sl] = kEmpty, vals[sl] = 0.0, flag[sl] = 0;
             }
             n_live += live;
@@ -299,30 +319,25 @@ merge_kernel(MergeArgs A) {
                 } else {
                     atomicOr(A.status, 8);
                 }
-                const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
-                if (vb << 1) {  // non-zero
-                    atomicAdd(&hist[(unsigned)((0x7fffffffffffffffull - (vb & 0x7fffffffffffffffull)) >> 51)], 1u);
-                    sq = __fma_rn(v, v, sq);
-                }
             }
         }
         __syncthreads();
         if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u);
         __syncthreads();
     }
-    for (int b = tid; b < kBins; b += kMT)
-        if (hist[b]) atomicAdd(&A.hist[b], (unsigned long long)hist[b]);
     for (int o = 16; o > 0; o >>= 1) {
         sq += __shfl_xor_sync(kFull, sq, o);
         n_live += __shfl_xor_sync(kFull, n_live, o);
+        n_nonzero += __shfl_xor_sync(kFull, n_nonzero, o);
     }
     if (lane == 0) {
         atomicAdd(A.sumsq, sq);
         atomicAdd(A.n_live, n_live);
+        atomicAdd(A.n_nonzero, n_nonzero);
     }
 }
 
-constexpr size_t merge_smem(int slots) { return size_t(slots) * (8 + 8 + 2 + 1) + size_t(kBins) * 4; }
+constexpr size_t merge_smem(int slots) { return size_t(slots) * (8 + 8 + 2 + 1); }
 
 // ------------------------------------------------------------- u entries
 
@@ -331,8 +346,8 @@ constexpr size_t merge_smem(int slots) { return size_t(slots) * (8 + 8 + 2 + 1) 
 // also holds are written as empty keys.
 __global__ void u_entries_kernel(VecRef wi, const double *sig_i, VecRef wm, const double *sig_m,
                                  double a, double b, unsigned long long *out_key, double *out_val,
-                                 unsigned long long base_n, long long out_cap,
-                                 unsigned long long *hist, double *sumsq, int *status) {
+                                 unsigned long long base_n, long long out_cap, double *sumsq,
+                                 int *status) {
     double sq = 0.0;
     const long long total = wi.n + wm.n;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -370,10 +385,7 @@ __global__ void u_entries_kernel(VecRef wi, const double *sig_i, VecRef wm, cons
         }
         out_key[pos] = valid ? key : kEmpty;
         out_val[pos] = valid ? u : 0.0;
-        if (valid && u != 0.0) {
-            atomicAdd(&hist[top12_bin(u)], 1ull);
-            sq = __fma_rn(u, u, sq);
-        }
+        if (valid && u != 0.0) sq = __fma_rn(u, u, sq);
     }
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
     if ((threadIdx.x & 31) == 0 && sq != 0.0) atomicAdd(sumsq, sq);
@@ -406,6 +418,23 @@ __global__ void aligned_finish_kernel(const double *partial, int np, double *out
         double r = 0.0;
         for (int k = 0; k < np; ++k) r += partial[(size_t)blockIdx.x * np + k];
         out[blockIdx.x] = r;
+    }
+}
+
+__global__ void min_abs_kernel(const double *val, const unsigned long long *n_dev, long long cap,
+                               double *out) {
+    __shared__ double sh[32];
+    long long n = (long long)*n_dev;
+    if (n > cap) n = cap;
+    double m = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) m = fmin(m, fabs(val[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = sh[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmin(r, sh[w]);
+        *out = r;
     }
 }
 
@@ -445,39 +474,46 @@ cudaError_t exclusive_scan(const unsigned *in, long long m, unsigned long long *
     return cudaGetLastError();
 }
 
-cudaError_t sort_overflow(const unsigned *count, unsigned lo, unsigned nb, unsigned cap,
+cudaError_t sort_overflow(const Buckets &bk, const unsigned *count, unsigned lo, unsigned nb,
                           const Slot *ovf, const unsigned long long *ovf_n, long long ovf_cap,
-                          int log2B, unsigned *tmp_counts, unsigned long long *off, void *scan_ws,
-                          Slot *out, cudaStream_t st) {
+                          unsigned *tmp_counts, unsigned long long *off, void *scan_ws, Slot *out,
+                          cudaStream_t st) {
     count_launch();
-    ovf_counts_kernel<<<grid_for(nb, 8), 256, 0, st>>>(count, lo, nb, cap, tmp_counts);
+    ovf_counts_kernel<<<grid_for(nb, 8), 256, 0, st>>>(bk.boff, count, lo, nb, tmp_counts);
     cudaError_t e = exclusive_scan(tmp_counts, nb, off, scan_ws, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(tmp_counts, 0, size_t(nb) * 4, st);
     if (e != cudaSuccess) return e;
     count_launch();
     ovf_scatter_kernel<<<grid_for(ovf_cap < (1 << 24) ? ovf_cap : (1 << 24), 8), 256, 0, st>>>(
-        ovf, ovf_n, ovf_cap, log2B, lo, off, tmp_counts, out);
+        bk, ovf, ovf_n, ovf_cap, lo, off, tmp_counts, out);
     return cudaGetLastError();
 }
 
-cudaError_t sort_probes(const VecRef *vecs, int nvec, int log2B, unsigned *pcount,
-                        unsigned long long *poff, void *scan_ws, Probe *out, cudaStream_t st) {
-    const unsigned long long B = 1ull << log2B;
+cudaError_t sort_probes(const Buckets &bk, unsigned long long nbuckets, const VecRef *vecs,
+                        double *const *sigw, int nvec, unsigned *pcount, unsigned long long *poff,
+                        void *scan_ws, Probe *out, cudaStream_t st) {
     VecPackRef vp{};
-    long long tot = 0;
-    for (int j = 0; j < nvec; ++j) vp.v[j] = vecs[j], tot += vecs[j].n;
-    cudaError_t e = cudaMemsetAsync(pcount, 0, B * 4, st);
+    SigPack sp{};
+    long long mx = 1;
+    for (int j = 0; j < nvec; ++j) vp.v[j] = vecs[j], sp.p[j] = sigw[j], mx = vecs[j].n > mx ? vecs[j].n : mx;
+    cudaError_t e = cudaMemsetAsync(pcount, 0, nbuckets * 4, st);
     if (e != cudaSuccess) return e;
     count_launch();
-    probe_count_kernel<<<grid_for(tot / (nvec > 0 ? nvec : 1) + 1, 8), 256, 0, st>>>(vp, nvec, log2B, pcount);
-    e = exclusive_scan(pcount, (long long)B, poff, scan_ws, st);
+    probe_count_kernel<<<grid_for(mx, 8), 256, 0, st>>>(bk, vp, sp, nvec, pcount);
+    e = exclusive_scan(pcount, (long long)nbuckets, poff, scan_ws, st);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(pcount, 0, B * 4, st);
+    e = cudaMemsetAsync(pcount, 0, nbuckets * 4, st);
     if (e != cudaSuccess) return e;
     count_launch();
-    probe_scatter_kernel<<<grid_for(tot / (nvec > 0 ? nvec : 1) + 1, 8), 256, 0, st>>>(
-        vp, nvec, log2B, poff, pcount, out);
+    probe_scatter_kernel<<<grid_for(mx, 8), 256, 0, st>>>(bk, vp, nvec, poff, pcount, out);
+    return cudaGetLastError();
+}
+
+cudaError_t uniform_offsets(unsigned long long *boff, unsigned long long nb, unsigned cap,
+                            cudaStream_t st) {
+    count_launch();
+    uniform_offsets_kernel<<<grid_for((long long)nb + 1, 8), 256, 0, st>>>(boff, nb, cap);
     return cudaGetLastError();
 }
 
@@ -510,13 +546,20 @@ cudaError_t launch_merge(const MergeArgs &A, int slots, cudaStream_t st) {
 
 cudaError_t launch_u_entries(VecRef wi, const double *sig_i, VecRef wm, const double *sig_m,
                              double a, double b, unsigned long long *out_key, double *out_val,
-                             unsigned long long base_n, long long out_cap, unsigned long long *hist,
-                             double *sumsq, int *status, cudaStream_t st) {
+                             unsigned long long base_n, long long out_cap, double *sumsq,
+                             int *status, cudaStream_t st) {
     const long long total = wi.n + wm.n;
     if (total <= 0) return cudaSuccess;
     count_launch();
     u_entries_kernel<<<grid_for(total, 8), 256, 0, st>>>(wi, sig_i, wm, sig_m, a, b, out_key, out_val,
-                                                         base_n, out_cap, hist, sumsq, status);
+                                                         base_n, out_cap, sumsq, status);
+    return cudaGetLastError();
+}
+
+cudaError_t min_abs(const double *val, const unsigned long long *n_dev, long long cap, double *out,
+                    cudaStream_t st) {
+    count_launch();
+    min_abs_kernel<<<1, 1024, 0, st>>>(val, n_dev, cap, out);
     return cudaGetLastError();
 }
 

@@ -249,32 +249,6 @@ __global__ void sel_stats_kernel(const SelState *s, double *sumsq_out, unsigned 
     }
 }
 
-__global__ void sel_load_hist_kernel(SelState *s, unsigned long long k, const unsigned long long *h0,
-                                     unsigned long long *hist, unsigned long long *n_out,
-                                     unsigned long long *cand_n) {
-    __shared__ unsigned long long part[kT];
-    unsigned long long t = 0;
-    for (int b = threadIdx.x; b < kBins; b += blockDim.x) {
-        hist[b] = h0[b];
-        t += h0[b];
-    }
-    part[threadIdx.x] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long tot = 0;
-        for (int q = 0; q < kT; ++q) tot += part[q];
-        s->pfx_hi = s->pfx_lo = s->mask_hi = s->mask_lo = 0ull;
-        s->need = k;
-        s->total = tot;
-        s->done = (k == 0);
-        s->all = 0;
-        s->pass = 0;
-        s->sumsq = 0.0;
-        *n_out = 0;
-        *cand_n = 0;
-    }
-}
-
 // one pass: items of a smaller first digit than the picked bin -> out; of the
 // picked bin -> cand (or out, when the bin is taken whole)
 __global__ void sel_split_kernel(Items it, const SelState *s, unsigned long long *out_key,
@@ -532,7 +506,7 @@ cudaError_t select_topk(Items it, long long k, unsigned long long *out_key, doub
     return cudaGetLastError();
 }
 
-cudaError_t select_split(Items it, long long k, const unsigned long long *hist0,
+cudaError_t select_split(Items it, long long k,
                          unsigned long long *out_key, double *out_val, unsigned long long *n_out_dev,
                          unsigned long long *cand_key, double *cand_val, long long cand_cap,
                          unsigned long long *cand_n, void *ws, size_t ws_bytes, SplitResult *res_host,
@@ -544,8 +518,11 @@ cudaError_t select_split(Items it, long long k, const unsigned long long *hist0,
     unsigned long long *hist = reinterpret_cast<unsigned long long *>(base + L.hist);
     SplitResult *r = reinterpret_cast<SplitResult *>(base + L.result);
     count_launch();
-    sel_load_hist_kernel<<<1, kT, 0, st>>>(s, (unsigned long long)(k < 0 ? 0 : k), hist0, hist,
-                                           n_out_dev, cand_n);
+    sel_init_kernel<<<1, kT, 0, st>>>(s, (unsigned long long)(k < 0 ? 0 : k), hist, n_out_dev);
+    cudaError_t e = cudaMemsetAsync(cand_n, 0, 8, st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    sel_hist_kernel<<<grid_for(it.n, 4), kT, 0, st>>>(it, s, hist, 0);
     count_launch();
     sel_pick_kernel<<<1, kT, 0, st>>>(s, hist, 0);
     count_launch();
@@ -553,7 +530,7 @@ cudaError_t select_split(Items it, long long k, const unsigned long long *hist0,
                                                        cand_key, cand_val, cand_cap, cand_n);
     count_launch();
     sel_split_result_kernel<<<1, 32, 0, st>>>(s, n_out_dev, cand_n, r);
-    cudaError_t e = cudaMemcpyAsync(res_host, r, sizeof(SplitResult), cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(res_host, r, sizeof(SplitResult), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(st);
 }
