@@ -104,15 +104,6 @@ constexpr int kU = 4;  // elements each lane carries per reservation round
 
 __device__ __forceinline__ bool in_pass(const BucketOut &B, unsigned b) { return b >= B.lo && b < B.hi; }
 
-// can any bucket of row ha be in this pass?  (row mode: a row's buckets are
-// contiguous; hash mode: always)
-__device__ __forceinline__ bool row_in_pass(const BucketOut &B, unsigned long long ha) {
-    if (!B.bk.rowmap) return true;
-    const unsigned long long m = __ldg(&B.bk.rowmap[ha]);
-    const unsigned ns = (unsigned)m, first = (unsigned)(m >> 32);
-    return ns > 0 && first < B.hi && first + ns > B.lo;
-}
-
 // Up to kU elements per lane (ok[k]) are appended to their buckets: the lanes
 // of the warp that share a bucket reserve their slots with one atomic, issued
 // for all k before any result is used, and write one run.
@@ -145,58 +136,132 @@ __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, 
     }
 }
 
+// bucket of a target whose alpha row is known ahead (first bucket and bucket
+// count of the row read once): ns == ~0 means hash mode (no row map)
+struct RowCtx {
+    unsigned first, ns;
+};
+
+__device__ __forceinline__ RowCtx row_ctx(const BucketOut &B, unsigned long long ha) {
+    if (!B.bk.rowmap) return RowCtx{0u, 0xffffffffu};
+    const unsigned long long m = __ldg(&B.bk.rowmap[ha]);
+    return RowCtx{(unsigned)(m >> 32), (unsigned)m};
+}
+
+// same value as bucket_ab(bk, ha, hb) for the row of rc
+__device__ __forceinline__ unsigned row_bucket(const Buckets &bk, RowCtx rc, unsigned long long ha,
+                                               unsigned long long hb) {
+    if (rc.ns == 0xffffffffu) {
+        const unsigned long long key = ha * bk.cb + hb;
+        return bk.log2B > 0 ? (unsigned)(mix64(key) >> (64 - bk.log2B)) : 0u;
+    }
+    if (rc.ns <= 1) return rc.ns ? rc.first : kNoBucket;
+    return rc.first + (unsigned)(((mix64(hb) >> 32) * rc.ns) >> 32);
+}
+
+// can any bucket of the row be in this pass?  A row without buckets means
+// the row weights missed it: status 16.
+__device__ __forceinline__ bool ctx_in_pass(const BucketOut &B, RowCtx rc) {
+    if (rc.ns == 0xffffffffu) return true;
+    if (rc.ns == 0) {
+        atomicOr(B.status, 16);
+        return false;
+    }
+    return rc.first < B.hi && rc.first + rc.ns > B.lo;
+}
+
+// target in this launch?  (bucket mode: its bucket b is in the pass)
+template <int kMode>
+__device__ __forceinline__ bool wanted(const EmitOut &o, unsigned long long ha, unsigned long long hb,
+                                       unsigned &b) {
+    if (kMode != kModeBucket) return true;
+    b = bucket_ab(o.b.bk, ha, hb);
+    if (b == kNoBucket) {
+        atomicOr(o.b.status, 16);
+        return false;
+    }
+    return in_pass(o.b, b);
+}
+
+template <int kMode>
+__device__ __forceinline__ bool row_wanted(const EmitOut &o, RowCtx rc, unsigned long long ha,
+                                           unsigned long long hb, unsigned &b) {
+    if (kMode != kModeBucket) return true;
+    b = row_bucket(o.b.bk, rc, ha, hb);
+    return in_pass(o.b, b);
+}
+
+// A round whose elements all go to bucket b (a row with one bucket): one
+// reservation for the whole warp, positions by ballot prefix.
+__device__ __forceinline__ void single_append(const BucketOut &B, unsigned b, const bool *ok,
+                                              const unsigned long long *tg, const double *v) {
+    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    unsigned pre[kU], tot = 0;
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+        const unsigned bal = __ballot_sync(kFull, ok[k]);
+        pre[k] = tot + __popc(bal & lt);
+        tot += __popc(bal);
+    }
+    if (tot == 0) return;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&B.count[b], tot);
+    base = __shfl_sync(kFull, base, 0);
+    const unsigned long long o0 = __ldg(&B.bk.boff[b]), cap = __ldg(&B.bk.boff[b + 1]) - o0;
+    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(B.elem) + (o0 - __ldg(&B.bk.boff[B.lo]));
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+        if (!ok[k]) continue;
+        const unsigned pos = base + pre[k];
+        const ulonglong2 sl = make_ulonglong2(tg[k], (unsigned long long)__double_as_longlong(v[k]));
+        if (pos < cap) {
+            dst[pos] = sl;
+        } else {
+            const unsigned long long q = atomicAdd(B.ovf_n, 1ull);
+            if ((long long)q < B.ovf_cap) reinterpret_cast<ulonglong2 *>(B.ovf)[q] = sl;
+            else atomicOr(B.status, 2);
+        }
+    }
+}
+
 // One round of the warp over up to kU elements per lane: element k of this
-// lane targets (ha[k], hb[k]) with unscaled value e[k] (only computed when
-// want[k]); debug and table modes deliver lane by lane.
+// lane targets (ha[k], hb[k]) in bucket bk[k] with unscaled value e[k] (only
+// computed when want[k]); debug and table modes deliver lane by lane.  With
+// single >= 0 every element of the round is in bucket `single`.
 template <int kMode>
 __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
                                            const unsigned long long *ha, const unsigned long long *hb,
-                                           const double *e, const long long *di, long long s, double c,
-                                           unsigned long long cb, unsigned &inserted) {
-    if (kMode == kModeDebug) {
+                                           const unsigned *bk, const double *e, const long long *di,
+                                           long long s, double c, unsigned long long cb,
+                                           unsigned &inserted, long long single = -1) {
+    if constexpr (kMode == kModeDebug) {
 #pragma unroll
         for (int k = 0; k < kU; ++k)
             if (want[k]) o.dsrc[di[k]] = s, o.dtgt[di[k]] = ha[k] * cb + hb[k], o.delem[di[k]] = e[k];
-        return;
-    }
-    if (kMode == kModeTable) {
+    } else if constexpr (kMode == kModeTable) {
 #pragma unroll
         for (int k = 0; k < kU; ++k) {
             if (!want[k]) continue;
             const double v = __dmul_rn(e[k], c);
             if (nonzero(v)) table_add(o.t, ha[k] * cb + hb[k], v, inserted);
         }
-        return;
-    }
-    bool ok[kU];
-    unsigned bk[kU];
-    unsigned long long tg[kU];
-    double v[kU];
+    } else {
+        bool ok[kU];
+        unsigned long long tg[kU];
+        double v[kU];
 #pragma unroll
-    for (int k = 0; k < kU; ++k) {
-        ok[k] = false;
-        bk[k] = 0;
-        tg[k] = 0;
-        v[k] = 0.0;
-        if (!want[k]) continue;
-        v[k] = __dmul_rn(e[k], c);
-        tg[k] = ha[k] * cb + hb[k];
-        bk[k] = bucket_ab(o.b.bk, ha[k], hb[k]);
-        ok[k] = nonzero(v[k]);
+        for (int k = 0; k < kU; ++k) {
+            ok[k] = false;
+            tg[k] = 0;
+            v[k] = 0.0;
+            if (!want[k]) continue;
+            v[k] = __dmul_rn(e[k], c);
+            tg[k] = ha[k] * cb + hb[k];
+            ok[k] = nonzero(v[k]);
+        }
+        if (single >= 0) single_append(o.b, (unsigned)single, ok, tg, v);
+        else warp_append(o.b, ok, bk, tg, v);
     }
-    warp_append(o.b, ok, bk, tg, v);
-}
-
-// target in this launch?  (bucket mode: its bucket is in the pass)
-template <int kMode>
-__device__ __forceinline__ bool wanted(const EmitOut &o, unsigned long long ha, unsigned long long hb) {
-    if (kMode != kModeBucket) return true;
-    const unsigned b = bucket_ab(o.b.bk, ha, hb);
-    if (b == kNoBucket) {
-        atomicOr(o.b.status, 16);
-        return false;
-    }
-    return in_pass(o.b, b);
 }
 
 // prefix sums A0 | A1 | A2 over the M - 2 electrons of str left after removing
@@ -298,34 +363,42 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             offB1[y] = unsigned(b * n + j) | (sg << 31);
         }
         __syncwarp();
-        const bool self_row = kMode != kModeBucket || row_in_pass(o.b, hA);
+        // the source's own row: first bucket and count read once
+        const RowCtx rs = kMode == kModeBucket ? row_ctx(o.b, hA) : RowCtx{0u, 0u};
+        const bool self_row = kMode != kModeBucket || ctx_in_pass(o.b, rs);
+        const long long self_single = kMode == kModeBucket && rs.ns == 1 ? (long long)rs.first : -1;
 
         bool want[kU];
         unsigned long long ha[kU], hb[kU];
+        unsigned bk[kU];
         double e[kU];
         long long di[kU];
-#define SFCI_CLEAR()                                      \
-    for (int k = 0; k < kU; ++k) want[k] = false, ha[k] = 0, hb[k] = 0, e[k] = 0.0, di[k] = 0;
+#define SFCI_CLEAR()                                                                          \
+    for (int k = 0; k < kU; ++k) want[k] = false, ha[k] = 0, hb[k] = 0, bk[k] = 0, e[k] = 0.0, di[k] = 0;
 
-        // diagonal (lane 0) and alpha singles
+        // diagonal (lane 0, in the oracle's term order)
+        unsigned dbk = 0;
+        const bool dwant = self_row && row_wanted<kMode>(o, rs, hA, hB, dbk);
+        const double ediag = dwant && lane == 0 ? diagonal_element(d, occA, occB) : 0.0;
+        // diagonal and alpha singles
         for (int x0 = -1; x0 < d.sa; x0 += 32 * kU) {
             SFCI_CLEAR();
 #pragma unroll
             for (int k = 0; k < kU; ++k) {
                 const int x = x0 + 32 * k + lane;
                 if (x == -1) {
-                    if (!self_row || !wanted<kMode>(o, hA, hB)) continue;
-                    want[k] = true, ha[k] = hA, hb[k] = hB, di[k] = base;
-                    e[k] = diagonal_element(d, occA, occB);
+                    if (!dwant) continue;
+                    want[k] = true, ha[k] = hA, hb[k] = hB, bk[k] = dbk, di[k] = base;
+                    e[k] = ediag;
                 } else if (x >= 0 && x < d.sa) {
-                    if (!wanted<kMode>(o, rankA1[x], hB)) continue;
+                    if (!wanted<kMode>(o, rankA1[x], hB, bk[k])) continue;
                     const int io = x / d.va, iv = x - io * d.va;
                     const double F = single_element(d, occA[io], virA[iv], occA, occB, occA, d.na);
                     want[k] = true, ha[k] = rankA1[x], hb[k] = hB, di[k] = base + 1 + x;
                     e[k] = flip(F, offA1[x] >> 31);
                 }
             }
-            emit_round<kMode>(o, want, ha, hb, e, di, s, c, cb, inserted);
+            emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted);
         }
         long long off = base + 1 + d.sa;
         // beta singles (all in row hA)
@@ -335,13 +408,13 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
 #pragma unroll
                 for (int k = 0; k < kU; ++k) {
                     const int y = y0 + 32 * k + lane;
-                    if (y >= d.sb || !wanted<kMode>(o, hA, rankB1[y])) continue;
+                    if (y >= d.sb || !row_wanted<kMode>(o, rs, hA, rankB1[y], bk[k])) continue;
                     const int jo = y / d.vb, jv = y - jo * d.vb;
                     const double F = single_element(d, occB[jo], virB[jv], occA, occB, occB, d.nb);
                     want[k] = true, ha[k] = hA, hb[k] = rankB1[y], di[k] = off + y;
                     e[k] = flip(F, offB1[y] >> 31);
                 }
-                emit_round<kMode>(o, want, ha, hb, e, di, s, c, cb, inserted);
+                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, self_single);
             }
         }
         off += d.sb;
@@ -371,7 +444,8 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                         const int a = vir[pv[2 * q]], b = vir[pv[2 * q + 1]];
                         const unsigned long long h2 = pair_rank(rem, a, b, M, pre, bt, ks);
                         const unsigned long long ta = spin ? hA : h2, tb = spin ? h2 : hB;
-                        if (!wanted<kMode>(o, ta, tb)) continue;
+                        if (spin ? !row_wanted<kMode>(o, rs, ta, tb, bk[k]) : !wanted<kMode>(o, ta, tb, bk[k]))
+                            continue;
                         const int s1 = parity64(str & between_mask(i, a));
                         const unsigned long long s1s = str ^ (1ull << i) ^ (1ull << a);
                         const int s2 = parity64(s1s & between_mask(j, b));
@@ -380,7 +454,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                                               __ldg(&g[(size_t(a * n + j) * n + b) * n + i])),
                                     unsigned(s1 ^ s2));
                     }
-                    emit_round<kMode>(o, want, ha, hb, e, di, s, c, cb, inserted);
+                    emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, spin ? self_single : -1);
                 }
                 __syncwarp();
             }
@@ -389,7 +463,9 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
         // opposite-spin doubles: alpha hop x (row rankA1[x]), beta hops y
         for (int x = 0; x < d.sa; ++x) {
             const unsigned long long ra = rankA1[x];
-            if (kMode == kModeBucket && !row_in_pass(o.b, ra)) continue;
+            const RowCtx rc = kMode == kModeBucket ? row_ctx(o.b, ra) : RowCtx{0u, 0u};
+            if (kMode == kModeBucket && !ctx_in_pass(o.b, rc)) continue;
+            const long long single = kMode == kModeBucket && rc.ns == 1 ? (long long)rc.first : -1;
             const unsigned oa = offA1[x];
             const double *gx = g + (oa & 0x7fffffffu);
             const unsigned sa = oa >> 31;
@@ -398,12 +474,12 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
 #pragma unroll
                 for (int k = 0; k < kU; ++k) {
                     const int y = y0 + 32 * k + lane;
-                    if (y >= d.sb || !wanted<kMode>(o, ra, rankB1[y])) continue;
+                    if (y >= d.sb || !row_wanted<kMode>(o, rc, ra, rankB1[y], bk[k])) continue;
                     const unsigned ob = offB1[y];
                     want[k] = true, ha[k] = ra, hb[k] = rankB1[y], di[k] = off + (long long)x * d.sb + y;
                     e[k] = flip(__ldg(&gx[ob & 0x7fffffffu]), sa ^ (ob >> 31));
                 }
-                emit_round<kMode>(o, want, ha, hb, e, di, s, c, cb, inserted);
+                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, single);
             }
         }
 #undef SFCI_CLEAR

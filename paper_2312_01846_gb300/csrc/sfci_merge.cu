@@ -32,18 +32,12 @@ namespace {
 
 constexpr int kMT = 256;             // merge CTA threads
 constexpr int kPre = 8;              // elements each thread loads before inserting
-constexpr int kBins = 4096;
 
 // slot in the shared-memory table: hash bits below those that chose the
 // bucket (hash mode); row mode uses the top bits
 template <int kSlots>
 __device__ __forceinline__ unsigned smem_slot(unsigned long long key, int log2B) {
     return (unsigned)(mix64(key) >> (64 - log2B - 13)) & (kSlots - 1);
-}
-
-__device__ __forceinline__ unsigned top12_bin(double v) {
-    const unsigned long long mag = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
-    return (unsigned)((0x7fffffffffffffffull - mag) >> 51);
 }
 
 // ------------------------------------------------------------- scan
