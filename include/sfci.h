@@ -140,6 +140,27 @@ sfci_status sfci_truncate_topk(const uint64_t *rank, const double *coef, int64_t
                                int normalize, uint64_t *out_rank, double *out_coef,
                                int64_t *n_out, void *workspace, size_t ws_bytes, void *stream);
 
+/* sfci_truncate_topk without a workspace, for callers that cannot allocate
+ * device memory (a host framework that owns all of it through its own pool, a
+ * plugin given a fixed budget, a loop that must not reach the allocator).
+ * The paper has no counterpart: this is a library convenience.  Same inputs,
+ * outputs, selection and errors as sfci_truncate_topk.
+ *   - Scratch: one fixed 20 MiB device array inside the library (one per
+ *     device), so k <= 1048576; a larger k returns SFCI_E_CAPACITY and the
+ *     reason in sfci_last_error().  n is not limited by the scratch.
+ *   - The call allocates nothing, neither does any kernel it launches.  It
+ *     clears the parts of the scratch that must start at zero itself.
+ *   - The first call on each device looks up the scratch's device address
+ *     (with that device current) and caches it; make that first call before
+ *     any stream capture.
+ *   - All calls on one device share the scratch: calls that overlap in time
+ *     (other threads, other streams) race and corrupt each other's results.
+ *     Serialise them.
+ *   - Synchronises the stream. */
+sfci_status sfci_truncate_topk_noalloc(const uint64_t *rank, const double *coef, int64_t n,
+                                       int64_t k, int normalize, uint64_t *out_rank,
+                                       double *out_coef, int64_t *n_out, void *stream);
+
 /* ---------------------------------------------------------- SFCI Lanczos */
 
 typedef struct sfci_params {

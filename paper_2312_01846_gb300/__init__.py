@@ -82,6 +82,8 @@ def lib():
         "sfci_truncate_topk_workspace_bytes": (_i32, [_i64, _i64, C.POINTER(C.c_size_t)]),
         "sfci_truncate_topk": (_i32, [_vp, _vp, _i64, _i64, _i32, _vp, _vp, C.POINTER(_i64), _vp,
                                       C.c_size_t, _vp]),
+        "sfci_truncate_topk_noalloc": (_i32, [_vp, _vp, _i64, _i64, _i32, _vp, _vp, C.POINTER(_i64),
+                                              _vp]),
         "sfci_lanczos_create": (_i32, [C.POINTER(_vp), _vp, C.POINTER(Params), _vp, _vp, _i64, _vp]),
         "sfci_lanczos_step": (_i32, [_vp, C.POINTER(StepInfo)]),
         "sfci_lanczos_vector": (_i32, [_vp, _vp, _vp, _i64, C.POINTER(_i64)]),
@@ -230,6 +232,28 @@ def sfci_truncate_topk(rank, coef, k, normalize=True, stream=None):
                                     _ptr(orank), _ptr(ocoef), C.byref(n), _ptr(ws), ws.numel(),
                                     _stream(stream)), "sfci_truncate_topk")
     return orank[: n.value], ocoef[: n.value]
+
+
+def sfci_truncate_topk_noalloc(rank, coef, k, normalize=True, out_rank=None, out_coef=None,
+                               stream=None):
+    """sfci_truncate_topk through the entry point that allocates nothing on the
+    device (fixed 20 MiB scratch inside the library, k <= 2^20).  Pass
+    out_rank/out_coef (device, >= k entries) to keep the call free of
+    allocations here too; calls that overlap in time must not share a device."""
+    r = _dev(rank, torch.int64)
+    c = _dev(coef, torch.float64)
+    k = int(k)
+    if out_rank is None:
+        out_rank = torch.empty(max(k, 1), dtype=torch.int64, device="cuda")
+    if out_coef is None:
+        out_coef = torch.empty(max(k, 1), dtype=torch.float64, device="cuda")
+    if out_rank.numel() < k or out_coef.numel() < k:
+        raise ValueError("output buffers need room for k entries")
+    n = C.c_int64()
+    _check(lib().sfci_truncate_topk_noalloc(_ptr(r), _ptr(c), r.numel(), k, int(bool(normalize)),
+                                            _ptr(out_rank), _ptr(out_coef), C.byref(n),
+                                            _stream(stream)), "sfci_truncate_topk_noalloc")
+    return out_rank[: n.value], out_coef[: n.value]
 
 
 def sfci_debug_excitations(sys: System, rank, stream=None):
