@@ -57,6 +57,10 @@ def parse():
                    help="intermediate elements per merge bucket (0 = automatic)")
     p.add_argument("--table-capacity", type=int, default=0,
                    help="merge-table slots (0 = sized by the solver)")
+    p.add_argument("--no-precision", action="store_true",
+                   help="skip the float32-element vs float64 comparison")
+    p.add_argument("--precision-nkeep", type=int, default=100_000)
+    p.add_argument("--precision-steps", type=int, default=30)
     return p.parse_args()
 
 
@@ -198,6 +202,45 @@ def run_reference(a):
 
 # ----------------------------------------------------------------- GPU arm
 
+def precision_study(sf, d, nkeep, n_lanczos, steps, stream):
+    """The solver from the aufbau determinant with float64 elements (twice) and
+    with SFCI_FP32_ELEMENTS: throughput of each and the energy difference at
+    every cycle end.  The second float64 run measures the run-to-run spread
+    (the merge's atomic adds fix no summation order, and the truncation
+    amplifies rounding-level differences), the floor against which the
+    float32 difference is read."""
+    import numpy as np
+    import torch
+    out = {}
+    for name, flags in (("f64", 0), ("f64_repeat", 0), ("fp32_elements", sf.SFCI_FP32_ELEMENTS)):
+        gsys = sf.System.from_dict(d, flags=flags)
+        lz = sf.Lanczos(gsys, np.array([0], dtype=np.uint64), np.array([1.0]), nkeep, n_lanczos,
+                        stream=stream)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        infos = [lz.step() for _ in range(steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        el = sum(i["n_elements"] for i in infos)
+        out[name] = {"elements_per_s": el / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "ms_sigma_mean": statistics.mean(i["ms_sigma"] for i in infos),
+                     "lambda": [i["lambda_min"] for i in infos if i["cycle_end"]]}
+        lz.close()
+        gsys.close()
+    lam64, lam32 = out["f64"]["lambda"], out["fp32_elements"]["lambda"]
+    out["delta_e_hartree"] = [b - a for a, b in zip(lam64, lam32)]
+    out["f64_repeat_delta_e_hartree"] = [b - a for a, b in zip(lam64, out["f64_repeat"]["lambda"])]
+    out["final_abs_delta_e_hartree"] = abs(out["delta_e_hartree"][-1]) if lam64 else None
+    out["within_1_uHa"] = out["final_abs_delta_e_hartree"] is not None and out["final_abs_delta_e_hartree"] <= 1e-6
+    out["speedup"] = out["fp32_elements"]["elements_per_s"] / out["f64"]["elements_per_s"]
+    out["workload"] = f"sfci-28o-7a7b-L200-clustered-Nd{nkeep:.0e}-NL{n_lanczos}".replace("+0", "") + \
+        f", {steps} steps from the aufbau determinant, both precisions"
+    return out
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -318,6 +361,10 @@ def run_ours(a):
                "sample": f"sigma of {a.cpu_sample} input determinants of a near-aufbau "
                          f"vector of the workload ({nel} elements, {dt:.1f} s)"}
 
+    precision = None
+    if rank == 0 and not a.no_precision:
+        precision = precision_study(sf, d, a.precision_nkeep, a.nlanczos, a.precision_steps, stream)
+
     last_lambda = [i["lambda_min"] for i in infos if i["cycle_end"]]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -329,6 +376,7 @@ def run_ours(a):
         "lanczos_steps_per_s": steps_per_s,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),
+        "precision": precision,
         "detail": {"n_in": infos[-1]["n_in"], "n_sigma": infos[-1]["n_sigma"],
                    "elements_per_step": el_per_launch, "lambda_min": last_lambda[-1] if last_lambda else None,
                    "ms_sigma_mean": ms_sig,

@@ -69,10 +69,20 @@ int64_t sfci_kernel_launches(void);
 
 typedef struct sfci_system sfci_system; /* opaque */
 
+/* sfci_system_create flags */
+/* Off-diagonal Slater-Condon elements (singles and doubles) from float32
+ * copies of h and g, with float32 sums for the singles.  The diagonal, the
+ * product element * c_D, the accumulation of sigma, the dots and the
+ * eigensolve stay float64.  Not in the paper (which works in float64): a
+ * precision option whose energy error against the float64 path is measured
+ * per result, not bounded a priori. */
+#define SFCI_FP32_ELEMENTS 1u
+
 /* Copy the integrals (host pointers; h: n*n, g: n^4 float64) to the current
  * device and build the binomial table C(b, m) used by Eq. 12.  n in [1, 64],
  * 0 <= n_alpha, n_beta <= n.  Returns SFCI_E_OVERFLOW when dim >= 2^64 - 1,
- * SFCI_E_INVALID for bad counts.  `flags` is reserved (pass 0). */
+ * SFCI_E_INVALID for bad counts or unknown flag bits.  flags: 0 or
+ * SFCI_FP32_ELEMENTS. */
 sfci_status sfci_system_create(sfci_system **out, int n_orb, int n_alpha, int n_beta,
                                const double *h_host, const double *g_host, double e_core,
                                uint32_t flags);
@@ -172,6 +182,10 @@ typedef struct sfci_params {
     int32_t max_iter;       /* the step that reaches this sigma count ends its cycle; <= 0 off */
     uint32_t flags;         /* reserved, pass 0                                      */
     int32_t bucket_elems;   /* intermediate elements per merge bucket; 0 = automatic */
+    int64_t mem_budget;     /* device bytes this solver's sigma buffers may take;
+                               0 = 85 % of what is free (one solver per device)   */
+    int32_t emit_warps;     /* warps per CTA of the element generator (1..8); 0 = 8 */
+    int32_t reserved;       /* pass 0                                                */
 } sfci_params;
 
 typedef struct sfci_step_info {

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsfci.so")
 
 SFCI_OK, SFCI_E_INVALID, SFCI_E_CAPACITY, SFCI_E_OVERFLOW = 0, 1, 2, 3
 SFCI_E_CUDA, SFCI_E_TIMEOUT, SFCI_E_NOMEM = 4, 5, 6
+SFCI_FP32_ELEMENTS = 1  # sfci_system_create flag: float32 off-diagonal elements
 
 
 class SfciError(RuntimeError):
@@ -32,7 +33,8 @@ class Params(C.Structure):
     _fields_ = [("n_keep", C.c_int64), ("table_capacity", C.c_int64),
                 ("eps_screen", C.c_double), ("conv_tol", C.c_double),
                 ("n_lanczos", C.c_int32), ("max_iter", C.c_int32),
-                ("flags", C.c_uint32), ("bucket_elems", C.c_int32)]
+                ("flags", C.c_uint32), ("bucket_elems", C.c_int32),
+                ("mem_budget", C.c_int64), ("emit_warps", C.c_int32), ("reserved", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -130,9 +132,11 @@ def _dev(x, dtype):
 class System:
     """Integrals + electron counts on the device (sfci_system_create)."""
 
-    def __init__(self, n, na, nb, h, g, e_core=0.0):
+    def __init__(self, n, na, nb, h, g, e_core=0.0, flags=0):
+        """flags: 0 or SFCI_FP32_ELEMENTS (float32 off-diagonal elements)."""
         import numpy as np
         self.n, self.na, self.nb = int(n), int(na), int(nb)
+        self.flags = int(flags)
         self._h = np.ascontiguousarray(np.asarray(h, dtype=np.float64).reshape(n, n))
         self._g = np.ascontiguousarray(np.asarray(g, dtype=np.float64).reshape(n, n, n, n))
         self.e_core = float(e_core)
@@ -140,7 +144,7 @@ class System:
         torch.cuda.init()
         _check(lib().sfci_system_create(C.byref(h_), self.n, self.na, self.nb,
                                         self._h.ctypes.data, self._g.ctypes.data,
-                                        self.e_core, 0), "sfci_system_create")
+                                        self.e_core, self.flags), "sfci_system_create")
         self.handle = h_
         d = C.c_uint64()
         _check(lib().sfci_dim(self.handle, C.byref(d)), "sfci_dim")
@@ -150,8 +154,8 @@ class System:
         self.n_conn = int(nc.value)
 
     @classmethod
-    def from_dict(cls, d):
-        return cls(d["n"], d["na"], d["nb"], d["h"], d["g"], d.get("e_core", 0.0))
+    def from_dict(cls, d, flags=0):
+        return cls(d["n"], d["na"], d["nb"], d["h"], d["g"], d.get("e_core", 0.0), flags)
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -311,12 +315,14 @@ class Lanczos:
     """The SFCI solver (sfci_lanczos_create / _step / _vector / _destroy)."""
 
     def __init__(self, sys: System, init_rank, init_coef, n_keep, n_lanczos=10, max_iter=0,
-                 eps_screen=0.0, conv_tol=0.0, table_capacity=0, bucket_elems=0, stream=None):
+                 eps_screen=0.0, conv_tol=0.0, table_capacity=0, bucket_elems=0, stream=None,
+                 mem_budget=0, emit_warps=0):
         self.sys = sys
         r = _dev(init_rank, torch.int64)
         c = _dev(init_coef, torch.float64)
         self.params = Params(int(n_keep), int(table_capacity), float(eps_screen), float(conv_tol),
-                             int(n_lanczos), int(max_iter), 0, int(bucket_elems))
+                             int(n_lanczos), int(max_iter), 0, int(bucket_elems),
+                             int(mem_budget), int(emit_warps), 0)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         _check(lib().sfci_lanczos_create(C.byref(h), sys.handle, C.byref(self.params), _ptr(r),

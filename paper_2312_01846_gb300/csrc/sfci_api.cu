@@ -116,25 +116,28 @@ int64_t sfci_kernel_launches(void) { return launch_count(); }
 
 sfci_status sfci_system_create(sfci_system **out, int n, int na, int nb, const double *h_host,
                                const double *g_host, double e_core, uint32_t flags) {
-    (void)flags;
     if (!out || !h_host || !g_host) return invalid("null argument");
+    if (flags & ~SFCI_FP32_ELEMENTS) return invalid("unknown flag bits");
+    const bool fp32 = (flags & SFCI_FP32_ELEMENTS) != 0;
     *out = nullptr;
     if (n < 1 || n > 64) {
         set_error("n_orb must be in [1, 64]");
         return SFCI_E_OVERFLOW;
     }
     if (na < 0 || nb < 0 || na > n || nb > n) return invalid("electron counts out of range");
-    // binomials C(b, m), b <= 64
-    static unsigned long long C[65][65];
-    static bool ready = false;
-    if (!ready) {
-        for (int a = 0; a <= 64; ++a) {
-            for (int b = 0; b <= 64; ++b) C[a][b] = 0;
-            C[a][0] = 1;
-            for (int b = 1; b <= a; ++b) C[a][b] = C[a - 1][b - 1] + C[a - 1][b];
+    // binomials C(b, m), b <= 64 (built once; thread-safe static initialisation)
+    struct Binomials {
+        unsigned long long v[65][65];
+        Binomials() {
+            for (int a = 0; a <= 64; ++a) {
+                for (int b = 0; b <= 64; ++b) v[a][b] = 0;
+                v[a][0] = 1;
+                for (int b = 1; b <= a; ++b) v[a][b] = v[a - 1][b - 1] + v[a - 1][b];
+            }
         }
-        ready = true;
-    }
+    };
+    static const Binomials binomials;
+    const auto &C = binomials.v;
     const unsigned long long ca = C[n][na], cb = C[n][nb];
     if (cb != 0 && ca > (~0ull - 1ull) / cb) {
         set_error("dim = C(n,na) C(n,nb) does not fit below 2^64 - 1");
@@ -177,6 +180,16 @@ sfci_status sfci_system_create(sfci_system **out, int n, int na, int nb, const d
     o = a256(o + bt.size() * 8);
     const size_t off_p = o;
     o = a256(o + pairs.size());
+    const size_t off_hf = o;
+    if (fp32) o = a256(o + nh * 4);
+    const size_t off_gf = o;
+    if (fp32) o = a256(o + ng * 4);
+    std::vector<float> hf, gf;
+    if (fp32) {
+        hf.resize(nh), gf.resize(ng);
+        for (size_t i = 0; i < nh; ++i) hf[i] = (float)h_host[i];
+        for (size_t i = 0; i < ng; ++i) gf[i] = (float)g_host[i];
+    }
     sfci_system *s = new (std::nothrow) sfci_system();
     if (!s) {
         set_error("host allocation failed");
@@ -195,6 +208,8 @@ sfci_status sfci_system_create(sfci_system **out, int n, int na, int nb, const d
     if (e == cudaSuccess) e = cudaMemcpy(blk + off_g, g_host, ng * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(blk + off_bt, bt.data(), bt.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(blk + off_p, pairs.data(), pairs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && fp32) e = cudaMemcpy(blk + off_hf, hf.data(), nh * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && fp32) e = cudaMemcpy(blk + off_gf, gf.data(), ng * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(blk);
         if (s->dev_status) cudaFree(s->dev_status);
@@ -205,6 +220,8 @@ sfci_status sfci_system_create(sfci_system **out, int n, int na, int nb, const d
     d.g = reinterpret_cast<const double *>(blk + off_g);
     d.binom = reinterpret_cast<const unsigned long long *>(blk + off_bt);
     d.pairs = reinterpret_cast<const unsigned char *>(blk + off_p);
+    d.hf = fp32 ? reinterpret_cast<const float *>(blk + off_hf) : nullptr;
+    d.gf = fp32 ? reinterpret_cast<const float *>(blk + off_gf) : nullptr;
     s->d = d;
     s->dev_block = blk;
     *out = s;

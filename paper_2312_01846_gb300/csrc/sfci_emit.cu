@@ -35,8 +35,14 @@ __host__ __device__ inline size_t block_smem(const SysDev &d) {
     return align16(size_t(d.n + 1) * d.ks * 8) + align16(size_t(d.n_pairs) * 2);
 }
 
+// per warp: rankA1, rankB1 (u64), prefix sums (192 u64), hopRC (u64 per alpha
+// hop), offA1, offB1 (u32), hopX (u16 per alpha hop), occupation lists (256 B)
 __host__ __device__ inline size_t warp_smem(const SysDev &d) {
-    return align16(size_t(d.sa + d.sb) * 12 + 192 * 8 + 256);
+    return align16(size_t(d.sa + d.sb) * 12 + size_t(d.sa) * 10 + 192 * 8 + 256);
+}
+
+inline size_t emit_smem_bytes_w(const SysDev &d, int warps) {
+    return block_smem(d) + size_t(warps) * warp_smem(d);
 }
 
 // single element h_ai + sum_{k occ alpha} (ai|kk) + sum_{k occ beta} (ai|kk)
@@ -62,6 +68,31 @@ __device__ __forceinline__ double single_element(const SysDev &d, int i, int a,
         v = __dsub_rn(v, __ldg(&d.g[(size_t(a * n + o) * n + o) * n + i]));
     }
     return v;
+}
+
+// the same single element from the float32 integral copies, float32 sums in
+// the same order (SFCI_FP32_ELEMENTS)
+__device__ __forceinline__ double single_element_f32(const SysDev &d, int i, int a,
+                                                     const unsigned char *occA,
+                                                     const unsigned char *occB,
+                                                     const unsigned char *occS, int ns) {
+    const int n = d.n;
+    const size_t n2 = size_t(n) * n;
+    const float *gai = d.gf + size_t(a * n + i) * n2;
+    float v = __ldg(&d.hf[a * n + i]);
+    for (int k = 0; k < d.na; ++k) {
+        int o = occA[k];
+        v = __fadd_rn(v, __ldg(&gai[o * n + o]));
+    }
+    for (int k = 0; k < d.nb; ++k) {
+        int o = occB[k];
+        v = __fadd_rn(v, __ldg(&gai[o * n + o]));
+    }
+    for (int k = 0; k < ns; ++k) {
+        int o = occS[k];
+        v = __fsub_rn(v, __ldg(&d.gf[(size_t(a * n + o) * n + o) * n + i]));
+    }
+    return (double)v;
 }
 
 // <D|H|D> = e_core + sum_k h_kk + 1/2 sum_{k,l} (kk|ll) - 1/2 sum_{k,l same spin} (kl|lk)
@@ -127,7 +158,7 @@ __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, 
         const unsigned long long o0 = __ldg(&B.bk.boff[bk[k]]), o1 = __ldg(&B.bk.boff[bk[k] + 1]);
         const ulonglong2 sl = make_ulonglong2(tg[k], (unsigned long long)__double_as_longlong(v[k]));
         if (pos < o1 - o0) {
-            reinterpret_cast<ulonglong2 *>(B.elem)[o0 - __ldg(&B.bk.boff[B.lo]) + pos] = sl;
+            reinterpret_cast<ulonglong2 *>(B.elem)[o0 - B.base + pos] = sl;
         } else {
             const unsigned long long q = atomicAdd(B.ovf_n, 1ull);
             if ((long long)q < B.ovf_cap) reinterpret_cast<ulonglong2 *>(B.ovf)[q] = sl;
@@ -208,7 +239,7 @@ __device__ __forceinline__ void single_append(const BucketOut &B, unsigned b, co
     if (lane == 0) base = atomicAdd(&B.count[b], tot);
     base = __shfl_sync(kFull, base, 0);
     const unsigned long long o0 = __ldg(&B.bk.boff[b]), cap = __ldg(&B.bk.boff[b + 1]) - o0;
-    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(B.elem) + (o0 - __ldg(&B.bk.boff[B.lo]));
+    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(B.elem) + (o0 - B.base);
 #pragma unroll
     for (int k = 0; k < kU; ++k) {
         if (!ok[k]) continue;
@@ -224,10 +255,27 @@ __device__ __forceinline__ void single_append(const BucketOut &B, unsigned b, co
     }
 }
 
+// the bucket of every wanted element of the round when they all share one,
+// -2 when the round has none, else -1 (every lane calls it)
+__device__ __forceinline__ long long round_single(const bool *want, const unsigned *bk) {
+    unsigned mine = kNoBucket;
+#pragma unroll
+    for (int k = 0; k < kU; ++k)
+        if (want[k] && mine == kNoBucket) mine = bk[k];
+    const unsigned has = __ballot_sync(kFull, mine != kNoBucket);
+    if (!has) return -2;
+    const unsigned ref = __shfl_sync(kFull, mine, __ffs(has) - 1);
+    bool diff = false;
+#pragma unroll
+    for (int k = 0; k < kU; ++k) diff |= want[k] && bk[k] != ref;
+    return __any_sync(kFull, diff) ? -1 : (long long)ref;
+}
+
 // One round of the warp over up to kU elements per lane: element k of this
 // lane targets (ha[k], hb[k]) in bucket bk[k] with unscaled value e[k] (only
 // computed when want[k]); debug and table modes deliver lane by lane.  With
-// single >= 0 every element of the round is in bucket `single`.
+// single >= 0 every element of the round is in bucket `single`; -2: the
+// round has no element.
 template <int kMode>
 __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
                                            const unsigned long long *ha, const unsigned long long *hb,
@@ -246,6 +294,7 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
             if (nonzero(v)) table_add(o.t, ha[k] * cb + hb[k], v, inserted);
         }
     } else {
+        if (single == -2) return;
         bool ok[kU];
         unsigned long long tg[kU];
         double v[kU];
@@ -321,15 +370,18 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
     unsigned long long *rankA1 = reinterpret_cast<unsigned long long *>(wb);
     unsigned long long *rankB1 = rankA1 + d.sa;
     unsigned long long *pre = rankB1 + d.sb;  // prefix sums A0 | A1 | A2, 64 each
-    unsigned *offA1 = reinterpret_cast<unsigned *>(pre + 192);
+    unsigned long long *hopRC = pre + 192;    // bucket map entry of each kept alpha hop's row
+    unsigned *offA1 = reinterpret_cast<unsigned *>(hopRC + d.sa);
     unsigned *offB1 = offA1 + d.sa;
-    unsigned char *occA = reinterpret_cast<unsigned char *>(offB1 + d.sb);
+    unsigned short *hopX = reinterpret_cast<unsigned short *>(offB1 + d.sb);  // kept alpha hops
+    unsigned char *occA = reinterpret_cast<unsigned char *>(hopX + d.sa);
     unsigned char *virA = occA + 64, *occB = occA + 128, *virB = occA + 192;
     const unsigned char *pOA = pairs + 2 * d.pair_off[0], *pVA = pairs + 2 * d.pair_off[1];
     const unsigned char *pOB = pairs + 2 * d.pair_off[2], *pVB = pairs + 2 * d.pair_off[3];
     const unsigned long long cb = d.cb;
     const double *__restrict__ g = d.g;
     const size_t n2 = size_t(n) * n;
+    const bool f32 = d.gf != nullptr;  // SFCI_FP32_ELEMENTS: off-diagonal elements in float32
 
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -363,6 +415,31 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             offB1[y] = unsigned(b * n + j) | (sg << 31);
         }
         __syncwarp();
+        // alpha hops whose target row can hold buckets of this pass (every hop
+        // outside bucket mode), compacted, with their row's bucket map entry
+        int m_hops = 0;
+        for (int x0 = 0; x0 < d.sa; x0 += 32) {
+            const int x = x0 + lane;
+            bool keep = false;
+            unsigned long long rcv = 0;
+            if (x < d.sa) {
+                if (kMode == kModeBucket) {
+                    const RowCtx rc = row_ctx(o.b, rankA1[x]);
+                    keep = ctx_in_pass(o.b, rc);
+                    rcv = (unsigned long long)rc.first << 32 | rc.ns;
+                } else {
+                    keep = true;
+                }
+            }
+            const unsigned bal = __ballot_sync(kFull, keep);
+            if (keep) {
+                const int pos = m_hops + __popc(bal & ((1u << lane) - 1u));
+                hopX[pos] = (unsigned short)x;
+                hopRC[pos] = rcv;
+            }
+            m_hops += __popc(bal);
+        }
+        __syncwarp();
         // the source's own row: first bucket and count read once
         const RowCtx rs = kMode == kModeBucket ? row_ctx(o.b, hA) : RowCtx{0u, 0u};
         const bool self_row = kMode != kModeBucket || ctx_in_pass(o.b, rs);
@@ -393,7 +470,8 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                 } else if (x >= 0 && x < d.sa) {
                     if (!wanted<kMode>(o, rankA1[x], hB, bk[k])) continue;
                     const int io = x / d.va, iv = x - io * d.va;
-                    const double F = single_element(d, occA[io], virA[iv], occA, occB, occA, d.na);
+                    const double F = f32 ? single_element_f32(d, occA[io], virA[iv], occA, occB, occA, d.na)
+                                         : single_element(d, occA[io], virA[iv], occA, occB, occA, d.na);
                     want[k] = true, ha[k] = rankA1[x], hb[k] = hB, di[k] = base + 1 + x;
                     e[k] = flip(F, offA1[x] >> 31);
                 }
@@ -410,7 +488,8 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     const int y = y0 + 32 * k + lane;
                     if (y >= d.sb || !row_wanted<kMode>(o, rs, hA, rankB1[y], bk[k])) continue;
                     const int jo = y / d.vb, jv = y - jo * d.vb;
-                    const double F = single_element(d, occB[jo], virB[jv], occA, occB, occB, d.nb);
+                    const double F = f32 ? single_element_f32(d, occB[jo], virB[jv], occA, occB, occB, d.nb)
+                                         : single_element(d, occB[jo], virB[jv], occA, occB, occB, d.nb);
                     want[k] = true, ha[k] = hA, hb[k] = rankB1[y], di[k] = off + y;
                     e[k] = flip(F, offB1[y] >> 31);
                 }
@@ -450,9 +529,11 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                         const unsigned long long s1s = str ^ (1ull << i) ^ (1ull << a);
                         const int s2 = parity64(s1s & between_mask(j, b));
                         want[k] = true, ha[k] = ta, hb[k] = tb, di[k] = off + (long long)p * npv + q;
-                        e[k] = flip(__dsub_rn(__ldg(&g[(size_t(a * n + i) * n + b) * n + j]),
-                                              __ldg(&g[(size_t(a * n + j) * n + b) * n + i])),
-                                    unsigned(s1 ^ s2));
+                        const size_t x1 = (size_t(a * n + i) * n + b) * n + j;
+                        const size_t x2 = (size_t(a * n + j) * n + b) * n + i;
+                        const double gd = f32 ? (double)__fsub_rn(__ldg(&d.gf[x1]), __ldg(&d.gf[x2]))
+                                              : __dsub_rn(__ldg(&g[x1]), __ldg(&g[x2]));
+                        e[k] = flip(gd, unsigned(s1 ^ s2));
                     }
                     emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, spin ? self_single : -1);
                 }
@@ -460,26 +541,35 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             }
             off += (long long)npo * npv;
         }
-        // opposite-spin doubles: alpha hop x (row rankA1[x]), beta hops y
-        for (int x = 0; x < d.sa; ++x) {
-            const unsigned long long ra = rankA1[x];
-            const RowCtx rc = kMode == kModeBucket ? row_ctx(o.b, ra) : RowCtx{0u, 0u};
-            if (kMode == kModeBucket && !ctx_in_pass(o.b, rc)) continue;
-            const long long single = kMode == kModeBucket && rc.ns == 1 ? (long long)rc.first : -1;
-            const unsigned oa = offA1[x];
-            const double *gx = g + (oa & 0x7fffffffu);
-            const unsigned sa = oa >> 31;
-            for (int y0 = 0; y0 < d.sb; y0 += 32 * kU) {
+        // opposite-spin doubles, flattened over (kept alpha hop, beta hop) pairs:
+        // lane t of the warp takes pairs t, t + 32, ... so every round is full
+        if (d.sb > 0 && m_hops > 0) {
+            const long long nab = (long long)m_hops * d.sb;
+            int cx = lane / d.sb;
+            int cy = lane - cx * d.sb;
+            for (long long t0 = 0; t0 < nab; t0 += 32 * kU) {
                 SFCI_CLEAR();
 #pragma unroll
                 for (int k = 0; k < kU; ++k) {
-                    const int y = y0 + 32 * k + lane;
-                    if (y >= d.sb || !row_wanted<kMode>(o, rc, ra, rankB1[y], bk[k])) continue;
-                    const unsigned ob = offB1[y];
-                    want[k] = true, ha[k] = ra, hb[k] = rankB1[y], di[k] = off + (long long)x * d.sb + y;
-                    e[k] = flip(__ldg(&gx[ob & 0x7fffffffu]), sa ^ (ob >> 31));
+                    if (t0 + 32 * k + lane < nab) {
+                        const int x = hopX[cx];
+                        const unsigned long long ra = rankA1[x], hbv = rankB1[cy];
+                        const unsigned long long rcv = hopRC[cx];
+                        const RowCtx rc{(unsigned)(rcv >> 32), (unsigned)rcv};
+                        if (row_wanted<kMode>(o, rc, ra, hbv, bk[k])) {
+                            const unsigned oa = offA1[x], ob = offB1[cy];
+                            const unsigned gi = (oa & 0x7fffffffu) + (ob & 0x7fffffffu);
+                            const double gv = f32 ? (double)__ldg(&d.gf[gi]) : __ldg(&g[gi]);
+                            want[k] = true, ha[k] = ra, hb[k] = hbv;
+                            di[k] = off + (long long)x * d.sb + cy;
+                            e[k] = flip(gv, (oa ^ ob) >> 31);
+                        }
+                    }
+                    cy += 32;
+                    while (cy >= d.sb) cy -= d.sb, ++cx;
                 }
-                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, single);
+                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted,
+                                  kMode == kModeBucket ? round_single(want, bk) : -1);
             }
         }
 #undef SFCI_CLEAR
@@ -596,32 +686,43 @@ int device_sms() {
     return sms > 0 ? sms : 1;
 }
 
+// warps per CTA: the requested count (0: 8), lowered until the CTA's shared
+// memory fits the device's per-block limit
+int emit_warps_for(const SysDev &d, int want) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int w = want > 0 && want < kEmitWarps ? want : kEmitWarps;
+    while (w > 1 && emit_smem_bytes_w(d, w) > (size_t)optin) --w;
+    return emit_smem_bytes_w(d, w) <= (size_t)optin ? w : 0;
+}
+
 template <int kMode>
 cudaError_t launch_emit_impl(const SysDev &d, const unsigned long long *in_rank,
                              const double *in_coef, long long n_in, const EmitOut &o,
-                             cudaStream_t st) {
+                             cudaStream_t st, int want_warps = 0) {
     if (n_in <= 0) return cudaSuccess;
-    const size_t smem = emit_smem_bytes(d, kEmitWarps);
+    const int warps = emit_warps_for(d, want_warps);
+    if (warps < 1) return cudaErrorInvalidConfiguration;  // one warp's tables exceed shared memory
+    const size_t smem = emit_smem_bytes_w(d, warps);
     auto kern = emit_kernel<kMode>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kEmitThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    long long want = (n_in + kEmitWarps - 1) / kEmitWarps;
+    long long want = (n_in + warps - 1) / warps;
     long long grid = (long long)device_sms() * per_sm;
     if (want < grid) grid = want;
     count_launch();
-    kern<<<(unsigned)grid, kEmitThreads, smem, st>>>(d, in_rank, in_coef, n_in, o);
+    kern<<<(unsigned)grid, warps * 32, smem, st>>>(d, in_rank, in_coef, n_in, o);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t emit_smem_bytes(const SysDev &d, int warps) {
-    return block_smem(d) + size_t(warps) * warp_smem(d);
-}
+size_t emit_smem_bytes(const SysDev &d, int warps) { return emit_smem_bytes_w(d, warps); }
 
 cudaError_t launch_emit(const SysDev &d, const unsigned long long *in_rank, const double *in_coef,
                         long long n_in, Table t, cudaStream_t st) {
@@ -632,10 +733,10 @@ cudaError_t launch_emit(const SysDev &d, const unsigned long long *in_rank, cons
 
 cudaError_t launch_emit_buckets(const SysDev &d, const unsigned long long *in_rank,
                                 const double *in_coef, long long n_in, const BucketOut &b,
-                                cudaStream_t st) {
+                                cudaStream_t st, int warps) {
     EmitOut o{};
     o.b = b;
-    return launch_emit_impl<kModeBucket>(d, in_rank, in_coef, n_in, o, st);
+    return launch_emit_impl<kModeBucket>(d, in_rank, in_coef, n_in, o, st, warps);
 }
 
 cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_rank, long long n_in,

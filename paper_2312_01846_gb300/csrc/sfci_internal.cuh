@@ -52,6 +52,8 @@ struct SysDev {
     const double *g;     // n^4
     const unsigned long long *binom;  // [(n+1) * ks]: C(b, m)
     const unsigned char *pairs;       // 2 bytes per pair: (first, second) positions, first < second
+    const float *hf;     // float32 copies of h and g (SFCI_FP32_ELEMENTS), else null
+    const float *gf;
 };
 
 }  // namespace sfci
@@ -217,6 +219,7 @@ struct BucketOut {
     Buckets bk;
     unsigned *count;          // [B] elements that arrived per bucket
     Slot *elem;               // regions of buckets [lo, hi), relative to boff[lo]
+    unsigned long long base;  // boff[lo]
     Slot *ovf;                // [ovf_cap]
     unsigned long long *ovf_n;
     long long ovf_cap;
@@ -266,7 +269,7 @@ cudaError_t launch_emit(const SysDev &d, const unsigned long long *in_rank,
                         const double *in_coef, long long n_in, Table t, cudaStream_t st);
 cudaError_t launch_emit_buckets(const SysDev &d, const unsigned long long *in_rank,
                                 const double *in_coef, long long n_in, const BucketOut &b,
-                                cudaStream_t st);
+                                cudaStream_t st, int warps = 0);
 // weights[ha] += intermediate elements bound for alpha string ha (enumerated,
 // zeros included), over all input determinants
 cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_rank, long long n_in,

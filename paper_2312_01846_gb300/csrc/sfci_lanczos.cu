@@ -392,7 +392,9 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double tau, unsigned long lon
         SFCI_CUDA(cudaMemGetInfo(&free_b, &tot_b));
         // memory the element regions may use: what is free plus what the big buffers hold
         const double held = (double)z->belem.bytes + (double)z->sig_key.bytes + (double)z->sig_val.bytes;
-        const double budget = 0.85 * ((double)free_b + held) - 1.1 * sig_need * 16.0 - 2.0 * ovf_cap * 16.0;
+        double avail = 0.85 * ((double)free_b + held);
+        if (z->p.mem_budget > 0) avail = std::min(avail, (double)z->p.mem_budget);
+        const double budget = avail - 1.1 * sig_need * 16.0 - 2.0 * ovf_cap * 16.0;
         // passes: contiguous bucket ranges whose regions fit the budget
         std::vector<unsigned long long> cuts{0};
         unsigned long long max_pass = 0;
@@ -461,13 +463,14 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double tau, unsigned long lon
             bo.bk = bk;
             bo.count = P<unsigned>(z->bcount);
             bo.elem = P<Slot>(z->belem);
+            bo.base = z->h_boff[lo];
             bo.ovf = P<Slot>(z->bovf);
             bo.ovf_n = z->ovf_n;
             bo.ovf_cap = z->ovf_cap;
             bo.lo = lo, bo.hi = hi;
             bo.status = z->mstatus;
             SFCI_CUDA(cudaEventRecord(z->evp[0], z->st));
-            SFCI_CUDA(launch_emit_buckets(d, z->wr[i], z->wc[i], n_in, bo, z->st));
+            SFCI_CUDA(launch_emit_buckets(d, z->wr[i], z->wc[i], n_in, bo, z->st, z->p.emit_warps));
             SFCI_CUDA(cudaEventRecord(z->evp[1], z->st));
             SFCI_CUDA(sort_overflow(bk, P<unsigned>(z->bcount), lo, hi - lo, P<Slot>(z->bovf), z->ovf_n,
                                     z->ovf_cap, P<unsigned>(z->tmp_counts), P<unsigned long long>(z->ovf_off),
@@ -581,6 +584,11 @@ sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
         set_error("need n_keep >= 1, 1 <= n_lanczos <= 64 and a non-empty trial vector");
         return SFCI_E_INVALID;
     }
+    if (params->emit_warps < 0 || params->emit_warps > 8 || params->mem_budget < 0 ||
+        params->bucket_elems < 0) {
+        set_error("need 0 <= emit_warps <= 8, mem_budget >= 0 and bucket_elems >= 0");
+        return SFCI_E_INVALID;
+    }
     sfci_lanczos *z = new (std::nothrow) sfci_lanczos();
     if (!z) return SFCI_E_NOMEM;
     z->sys = sys;
@@ -639,7 +647,9 @@ sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
     z->dS = z->dT + kMaxVec;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    unsigned long long bud = (unsigned long long)(0.8 * (double)free_b) / sizeof(Slot);
+    double table_bytes = 0.8 * (double)free_b;
+    if (params->mem_budget > 0) table_bytes = std::min(table_bytes, 0.5 * (double)params->mem_budget);
+    unsigned long long bud = (unsigned long long)table_bytes / sizeof(Slot);
     unsigned long long p2 = 1;
     while ((p2 << 1) <= bud) p2 <<= 1;
     z->budget = p2;

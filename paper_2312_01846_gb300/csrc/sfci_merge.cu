@@ -30,7 +30,10 @@
 namespace sfci {
 namespace {
 
-constexpr int kMT = 256;             // merge CTA threads
+#ifndef SFCI_MERGE_THREADS
+#define SFCI_MERGE_THREADS 256
+#endif
+constexpr int kMT = SFCI_MERGE_THREADS;  // merge CTA threads
 constexpr int kPre = 8;              // elements each thread loads before inserting
 
 // slot in the shared-memory table: hash bits below those that chose the
@@ -38,6 +41,10 @@ constexpr int kPre = 8;              // elements each thread loads before insert
 template <int kSlots>
 __device__ __forceinline__ unsigned smem_slot(unsigned long long key, int log2B) {
     return (unsigned)(mix64(key) >> (64 - log2B - 13)) & (kSlots - 1);
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
 
 // ------------------------------------------------------------- scan
@@ -205,6 +212,8 @@ merge_kernel(MergeArgs A) {
     __shared__ unsigned cur, n_occ;
     const int tid = threadIdx.x, lane = tid & 31;
     const bool screen = A.eps > 0.0;
+    // thresholds compared on bit patterns (|x| < t for t >= 0, NaN never below)
+    const unsigned long long eps_bits = abs_bits(A.eps), tau_bits = abs_bits(A.tau);
     for (int sl = tid; sl < kSlots; sl += kMT) keys[sl] = kEmpty, vals[sl] = 0.0, flag[sl] = 0;
     if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u);
     double sq = 0.0;
@@ -232,27 +241,46 @@ merge_kernel(MergeArgs A) {
                 x[k] = make_ulonglong2(kEmpty, 0ull);
                 if (e < total) x[k] = e < n_main ? src[e] : ovs[e - n_main];
             }
+            const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
             for (int k = 0; k < kPre; ++k) {
+                if (e0 + (unsigned)k * kMT >= total) break;  // block-uniform: no elements left
                 const unsigned long long key = x[k].x;
-                if (key == kEmpty) continue;
-                unsigned h = smem_slot<kSlots>(key, A.bk.rowmap ? 0 : A.bk.log2B);
-                int probe = 0;
-                for (; probe < kSlots; ++probe) {
-                    const unsigned long long c = keys[h];
-                    if (c == key) break;
-                    if (c == kEmpty) {
-                        const unsigned long long old = atomicCAS(&keys[h], kEmpty, key);
-                        if (old == kEmpty) {
-                            occ[atomicAdd(&n_occ, 1u)] = (unsigned short)h;
+                const bool act = key != kEmpty;
+                unsigned h = 0;
+                bool ins = false, found = false;
+                if (act) {
+                    h = smem_slot<kSlots>(key, A.bk.rowmap ? 0 : A.bk.log2B);
+                    for (int probe = 0; probe < kSlots; ++probe) {
+                        const unsigned long long c = keys[h];
+                        if (c == key) {
+                            found = true;
                             break;
                         }
-                        if (old == key) break;
+                        if (c == kEmpty) {
+                            const unsigned long long old = atomicCAS(&keys[h], kEmpty, key);
+                            if (old == kEmpty || old == key) {
+                                ins = old == kEmpty;
+                                found = true;
+                                break;
+                            }
+                        }
+                        h = (h + 1) & (kSlots - 1);
                     }
-                    h = (h + 1) & (kSlots - 1);
                 }
-                if (probe < kSlots) atomicAdd(&vals[h], __longlong_as_double((long long)x[k].y));
-                else atomicOr(A.status, 4);
+                // newly occupied slots: one list reservation per warp
+                const unsigned bal = __ballot_sync(kFull, ins);
+                if (bal) {
+                    const int leader = __ffs(bal) - 1;
+                    unsigned base = 0;
+                    if (lane == leader) base = atomicAdd(&n_occ, (unsigned)__popc(bal));
+                    base = __shfl_sync(kFull, base, leader);
+                    if (ins) occ[base + __popc(bal & lt)] = (unsigned short)h;
+                }
+                if (act) {
+                    if (found) atomicAdd(&vals[h], __longlong_as_double((long long)x[k].y));
+                    else atomicOr(A.status, 4);
+                }
             }
         }
         __syncthreads();
@@ -272,7 +300,7 @@ merge_kernel(MergeArgs A) {
                 h = (h + 1) & (kSlots - 1);
             }
             double sv = found >= 0 ? vals[found] : 0.0;
-            if (screen && fabs(sv) < A.eps) sv = 0.0;  // screened entries count as absent
+            if (screen && abs_bits(sv) < eps_bits) sv = 0.0;  // screened entries count as absent
             const int j = (int)(pr.where >> 40);
             const long long k = (long long)(pr.where & ((1ull << 40) - 1));
             A.sigw[j][k] = sv;
@@ -291,13 +319,14 @@ merge_kernel(MergeArgs A) {
                 const unsigned sl = occ[t];
                 key = keys[sl];
                 v = vals[sl];
-                live = !(screen && fabs(v) < A.eps);
-                const bool nz = live && !flag[sl] && (((unsigned long long)__double_as_longlong(v) << 1) != 0ull);
+                const unsigned long long ab = abs_bits(v);
+                live = !(screen && ab < eps_bits);
+                const bool nz = live && !flag[sl] && ab != 0ull;
                 if (nz) {
                     ++n_nonzero;
                     sq = __fma_rn(v, v, sq);
                 }
-                w = nz && !(fabs(v) < A.tau);
+                w = nz && !(ab < tau_bits);
                 keys[sl] = kEmpty, vals[sl] = 0.0, flag[sl] = 0;
             }
             n_live += live;
