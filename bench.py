@@ -57,6 +57,8 @@ def parse():
                    help="intermediate elements per merge bucket (0 = automatic)")
     p.add_argument("--table-capacity", type=int, default=0,
                    help="merge-table slots (0 = sized by the solver)")
+    p.add_argument("--emit-warps", type=int, default=0,
+                   help="warps per CTA of the element generator (0 = 8)")
     p.add_argument("--no-precision", action="store_true",
                    help="skip the float32-element vs float64 comparison")
     p.add_argument("--precision-nkeep", type=int, default=100_000)
@@ -264,10 +266,11 @@ def run_ours(a):
     gsys = sf.System.from_dict(d)
     stream = torch.cuda.current_stream()
     lz = sf.Lanczos(gsys, np.array([0], dtype=np.uint64), np.array([1.0]), a.nkeep, a.nlanczos,
-                    table_capacity=a.table_capacity, bucket_elems=a.bucket_elems, stream=stream)
+                    table_capacity=a.table_capacity, bucket_elems=a.bucket_elems, stream=stream,
+                    emit_warps=a.emit_warps)
     def brief(i):
         return {k: i[k] for k in ("n_in", "n_sigma", "n_passes", "ms_plan", "ms_emit", "ms_merge",
-                                  "ms_topk", "ms_step")}
+                                  "ms_topk", "ms_step", "redo", "tau", "cut")}
 
     warm = []
     for _ in range(a.warmup):

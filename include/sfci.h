@@ -213,6 +213,11 @@ typedef struct sfci_step_info {
     double ms_topk;    /* device time of the truncation (u entries, top-k, sort)    */
     int32_t n_passes;  /* passes over the sources that sigma needed (memory bound)  */
     int32_t n_buckets_log2; /* ceil(log2(merge buckets))                            */
+    double tau;        /* stream threshold of the accepted attempt (entries of sigma
+                          below it were not written out; see sfci_lanczos_step)  */
+    double cut;        /* |coef| of the N_d-th kept entry of u (0 if fewer kept)    */
+    int32_t redo;      /* sigma recomputed because tau hid part of the N_d largest  */
+    int32_t reserved;
 } sfci_step_info;
 
 typedef struct sfci_lanczos sfci_lanczos; /* opaque; owns w_0..w_{N_L-1}, T, S, table */
@@ -230,7 +235,12 @@ sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
  *   (Eqs. 10-11), or, at the cycle's last vector, the lowest root of
  *   T x = lambda S x, Psi = sum_j x_j w_j, and w_0 = normalise(top_{N_d}(Psi)).
  * info (host) receives the step's scalars.  Synchronises the solver's stream.
- * SFCI_E_CAPACITY only if sigma's table cannot grow in device memory. */
+ * Only the entries of u that can be among the N_d largest leave the merge:
+ * those with |u| >= tau, tau predicted from earlier cuts.  The step then checks
+ * that the N_d-th kept |u| is >= tau; if not, it recomputes sigma with the
+ * exact threshold read off a magnitude histogram of this attempt (info->redo),
+ * so the kept set is the exact top-N_d of Eq. 11 either way.
+ * SFCI_E_CAPACITY only if sigma's buffers cannot grow in device memory. */
 sfci_status sfci_lanczos_step(sfci_lanczos *lz, sfci_step_info *info);
 /* Restart the solver from a new trial vector (device pointers, ranks strictly
  * ascending): it is truncated to n_keep and normalised into w_0, and a new
@@ -246,6 +256,35 @@ sfci_status sfci_lanczos_vector(const sfci_lanczos *lz, uint64_t *rank, double *
  * upper triangle j <= i filled). */
 sfci_status sfci_lanczos_matrices(const sfci_lanczos *lz, double *T, double *S);
 sfci_status sfci_lanczos_destroy(sfci_lanczos *lz);
+
+/* ---------------------------------------------------------- batched scan */
+
+/* Many independent SFCI problems advanced together, e.g. a scan along a
+ * geometry-like parameter with uneven orbital counts, electron counts and
+ * N_d.  Not in the paper (which solves one system at a time): a runtime for
+ * running its method on many systems at once on one GPU.
+ *   count instances; systems[i] (all on one device), params[i] and the trial
+ *   vector (init_rank[i], init_coef[i], n_init[i], device pointers, ranks
+ *   strictly ascending) as for sfci_lanczos_create.  params[i].mem_budget = 0
+ *   gives instance i a share of 80 % of the free device memory in proportion
+ *   to N_d (n_conn + 1).  workers = host threads (0: min(count, 8)).
+ * Each instance runs on its own non-blocking stream; the scan owns the
+ * solvers and streams.  The systems must outlive the scan. */
+typedef struct sfci_scan sfci_scan;
+sfci_status sfci_scan_create(sfci_scan **out, int32_t count, const sfci_system *const *systems,
+                             const sfci_params *params, const uint64_t *const *init_rank,
+                             const double *const *init_coef, const int64_t *n_init,
+                             int32_t workers);
+/* One sfci_lanczos_step of every instance (Sec. 2.1, Eqs. 10-11 as there),
+ * run concurrently: worker threads take instances from a queue, largest
+ * expected work first.  infos (host, count entries) receives each instance's
+ * step information.  Returns the first failing instance's status (its index
+ * in sfci_last_error()); the other instances still completed their step. */
+sfci_status sfci_scan_step(sfci_scan *scan, sfci_step_info *infos);
+/* The solver of instance i (owned by the scan), for sfci_lanczos_vector and
+ * sfci_lanczos_matrices.  Do not step or destroy it directly. */
+sfci_status sfci_scan_solver(sfci_scan *scan, int32_t i, sfci_lanczos **out);
+sfci_status sfci_scan_destroy(sfci_scan *scan);
 
 /* ---------------------------------------------------------- density matrices */
 

@@ -47,7 +47,8 @@ class StepInfo(C.Structure):
                 ("ms_sigma", C.c_double), ("ms_step", C.c_double),
                 ("ms_emit", C.c_double), ("ms_merge", C.c_double),
                 ("ms_plan", C.c_double), ("ms_topk", C.c_double),
-                ("n_passes", C.c_int32), ("n_buckets_log2", C.c_int32)]
+                ("n_passes", C.c_int32), ("n_buckets_log2", C.c_int32),
+                ("tau", C.c_double), ("cut", C.c_double), ("redo", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,6 +95,11 @@ def lib():
         "sfci_rdm12_workspace_bytes": (_i32, [_vp, _i64, C.POINTER(C.c_size_t)]),
         "sfci_rdm12": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, C.POINTER(_f64), _vp, C.c_size_t, _vp]),
         "sfci_debug_excitations": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, C.POINTER(_i64), _vp]),
+        "sfci_scan_create": (_i32, [C.POINTER(_vp), _i32, C.POINTER(_vp), C.POINTER(Params),
+                                    C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_i64), _i32]),
+        "sfci_scan_step": (_i32, [_vp, C.POINTER(StepInfo)]),
+        "sfci_scan_solver": (_i32, [_vp, _i32, C.POINTER(_vp)]),
+        "sfci_scan_destroy": (_i32, [_vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -363,6 +369,58 @@ class Lanczos:
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             lib().sfci_lanczos_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scan:
+    """Many SFCI problems advanced together (sfci_scan_*): one step runs one
+    sfci_lanczos_step of every instance, concurrently, each on its own stream.
+
+    instances: list of (System, init_rank, init_coef, n_keep) tuples."""
+
+    def __init__(self, instances, n_lanczos=10, max_iter=0, eps_screen=0.0, bucket_elems=0,
+                 emit_warps=0, workers=0):
+        k = len(instances)
+        self.systems = [inst[0] for inst in instances]
+        self._vecs = [(_dev(inst[1], torch.int64), _dev(inst[2], torch.float64)) for inst in instances]
+        self.params = (Params * k)(*[
+            Params(int(inst[3]), 0, float(eps_screen), 0.0, int(n_lanczos), int(max_iter), 0,
+                   int(bucket_elems), 0, int(emit_warps), 0) for inst in instances])
+        torch.cuda.synchronize()
+        sysh = (_vp * k)(*[s.handle.value for s in self.systems])
+        rk = (_vp * k)(*[r.data_ptr() for r, _ in self._vecs])
+        cf = (_vp * k)(*[c.data_ptr() for _, c in self._vecs])
+        nn = (_i64 * k)(*[r.numel() for r, _ in self._vecs])
+        h = C.c_void_p()
+        _check(lib().sfci_scan_create(C.byref(h), k, sysh, self.params, rk, cf, nn, int(workers)),
+               "sfci_scan_create")
+        self.handle = h
+        self.count = k
+
+    def step(self):
+        infos = (StepInfo * self.count)()
+        _check(lib().sfci_scan_step(self.handle, infos), "sfci_scan_step")
+        return [x.as_dict() for x in infos]
+
+    def vector(self, i):
+        z = C.c_void_p()
+        _check(lib().sfci_scan_solver(self.handle, int(i), C.byref(z)), "sfci_scan_solver")
+        cap = int(self.params[i].n_keep)
+        r = torch.empty(cap, dtype=torch.int64, device="cuda")
+        c = torch.empty(cap, dtype=torch.float64, device="cuda")
+        n = C.c_int64()
+        _check(lib().sfci_lanczos_vector(z, _ptr(r), _ptr(c), cap, C.byref(n)), "sfci_lanczos_vector")
+        return r[: n.value], c[: n.value]
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().sfci_scan_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -338,13 +338,26 @@ struct MergeArgs {
     double *out_val;
     long long out_cap;
     unsigned long long *out_n;
-    double tau;                         // stream out only |u| >= tau (0: every non-zero entry)
+    // Stream threshold, raised while the merge runs: bit pattern of a
+    // non-negative double (|u| >= it is streamed out); hist counts the streamed
+    // entries by magnitude bin; when out_n passes *mark one CTA (holding *lock)
+    // raises it to the highest bin edge that still has nkeep streamed entries
+    // at or above it, and moves *mark halfway to out_cap.
+    unsigned long long *tau_bits;
+    unsigned long long *hist;           // [kHistBins]
+    unsigned long long *mark;
+    int *lock;
+    long long nkeep;
     double *sumsq;                      // sum of u^2 over the non-zero entries off w_i, w_{i-1}
     unsigned long long *n_live;         // entries that survive the screen
     unsigned long long *n_nonzero;      // non-zero entries off w_i, w_{i-1} (streamed or not)
     unsigned *queue;
     int *status;                        // bit 2: a bucket has too many distinct keys; bit 3: output full
 };
+// magnitude bins of |u|: the top 14 bits of the IEEE bit pattern (11 exponent
+// bits, 2 mantissa bits: quarter octaves) of a non-negative double
+constexpr int kHistShift = 50;
+constexpr int kHistBins = 1 << (63 - kHistShift);
 size_t scan_ws_bytes(long long m);
 cudaError_t exclusive_scan(const unsigned *in, long long m, unsigned long long *out, void *ws,
                            cudaStream_t st);

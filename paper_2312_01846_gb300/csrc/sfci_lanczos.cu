@@ -179,7 +179,7 @@ struct sfci_lanczos {
     std::vector<unsigned long long> h_weights, h_map, h_boff;
     long long sig_cap = 0, ovf_cap = 0, cand_cap = 0;
     double *sigw[kMaxVec] = {};
-    char *words = nullptr;  // hist[4096] | outn | mlive | ovf_n | cand_n | msumsq | queue | mstatus
+    char *words = nullptr;  // hist[kHistBins] | outn | mlive | ovf_n | cand_n | msumsq | queue | mstatus | nnz | dmin | tau | mark | lock
     unsigned long long *hist = nullptr, *outn = nullptr, *mlive = nullptr, *ovf_n = nullptr,
                        *cand_n = nullptr;
     double *msumsq = nullptr;
@@ -187,8 +187,11 @@ struct sfci_lanczos {
     int *mstatus = nullptr;
     double ms_emit = 0, ms_merge = 0, ms_plan = 0, budget_gb = 0;
     double tau_prev = 0.0;             // previous truncation cut in u (0: none)
+    std::vector<double> cut_at;        // truncation cut at each basis index of the last cycle
     unsigned long long stream_prev = 0;  // entries streamed by the previous merge
     unsigned long long *nnz = nullptr;  // device word: non-zero entries off w_i, w_{i-1}
+    unsigned long long *tau_w = nullptr, *mark_w = nullptr;  // stream threshold bits, raise mark
+    int *lock_w = nullptr;
     double *dmin = nullptr;             // device word: min |kept|
     int n_passes = 0, nb_log2 = 0;
 };
@@ -297,8 +300,9 @@ constexpr unsigned long long kMaxRows = 1ull << 26;
 // sigma_i = H w_i through the bucketed merge, with the probes of w_0..w_i.
 // On return the streamed entries sit in sig_key/sig_val[0, *n_out) and sigma at
 // every basis entry in sigw[j].
-sfci_status bucketed_sigma(sfci_lanczos *z, int i, double tau, unsigned long long *n_out,
+sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long long *n_out,
                            unsigned long long *n_live, unsigned long long *n_nonzero, double *sumsq) {
+    double tau = *tau_io;
     const SysDev &d = z->sys->d;
     const long long n_in = z->wn[i];
     const double E = (double)n_in * (double)(d.n_conn + 1);
@@ -448,7 +452,15 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double tau, unsigned long lon
         SFCI_CUDA(sort_probes(bk, B, vr.data(), z->sigw, i + 1, P<unsigned>(z->pcount),
                               P<unsigned long long>(z->poff), z->scan_ws.p, P<Probe>(z->probes), z->st));
         SFCI_CUDA(cudaMemsetAsync(z->bcount.p, 0, B * 4, z->st));
-        SFCI_CUDA(cudaMemsetAsync(z->words, 0, 4096 * 8 + 1024, z->st));
+        SFCI_CUDA(cudaMemsetAsync(z->words, 0, kHistBins * 8 + 1024, z->st));
+        // stream threshold (raised by the merge) and its first raise mark: half
+        // of the room left for streamed entries once u's entries are set aside
+        const long long u_room = 2 * z->nkeep + 1024;
+        const long long out_cap = std::max<long long>(z->sig_cap - u_room, 0);
+        unsigned long long tw[2];
+        std::memcpy(&tw[0], &tau, 8);
+        tw[1] = (unsigned long long)out_cap / 2;
+        SFCI_CUDA(cudaMemcpyAsync(z->tau_w, tw, 16, cudaMemcpyHostToDevice, z->st));
         SFCI_CUDA(cudaStreamSynchronize(z->st));
         z->ms_plan = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan0).count();
         z->budget_gb = budget / 1e9;
@@ -491,9 +503,13 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double tau, unsigned long lon
             A.eps = z->p.eps_screen > 0.0 ? z->p.eps_screen : 0.0;
             A.out_key = P<unsigned long long>(z->sig_key);
             A.out_val = P<double>(z->sig_val);
-            A.out_cap = z->sig_cap;
+            A.out_cap = out_cap;
             A.out_n = z->outn;
-            A.tau = tau;
+            A.tau_bits = z->tau_w;
+            A.hist = z->hist;
+            A.mark = z->mark_w;
+            A.lock = z->lock_w;
+            A.nkeep = z->nkeep;
             A.sumsq = z->msumsq;
             A.n_live = z->mlive;
             A.n_nonzero = z->nnz;
@@ -515,7 +531,11 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double tau, unsigned long lon
         SFCI_CUDA(cudaMemcpyAsync(&hl, z->mlive, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaMemcpyAsync(&hz, z->nnz, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaMemcpyAsync(&hq, z->msumsq, 8, cudaMemcpyDeviceToHost, z->st));
+        unsigned long long tb = 0;
+        SFCI_CUDA(cudaMemcpyAsync(&tb, z->tau_w, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaStreamSynchronize(z->st));
+        std::memcpy(&tau, &tb, 8);  // as raised during the merge
+        *tau_io = tau;
         if (hs == 0) {
             *n_out = ho, *n_live = hl, *n_nonzero = hz, *sumsq = hq;
             z->stream_prev = ho;
@@ -530,6 +550,8 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double tau, unsigned long lon
             return SFCI_E_CAPACITY;
         }
         if (hs & 2) ovf_cap *= 4;
+        // the stream outgrew its buffer before the raises caught up: redo from the
+        // raised threshold (still at or below the N_d-th largest) with more room
         if (hs & 8) sig_need = std::max(sig_need * 2.0, (double)ho * 1.3 + 2.0 * z->nkeep);
     }
     set_error("bucketed sigma did not fit after 8 attempts");
@@ -617,10 +639,10 @@ sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
     if (e == cudaSuccess) e = cudaMalloc(&z->scratch, o);
     for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&z->ev[k]);
     for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&z->evp[k]);
-    if (e == cudaSuccess) e = cudaMalloc(&z->words, 4096 * 8 + 1024);
+    if (e == cudaSuccess) e = cudaMalloc(&z->words, kHistBins * 8 + 1024);
     if (e == cudaSuccess) {
         z->hist = reinterpret_cast<unsigned long long *>(z->words);
-        char *w = z->words + 4096 * 8;
+        char *w = z->words + kHistBins * 8;
         z->outn = reinterpret_cast<unsigned long long *>(w);
         z->mlive = reinterpret_cast<unsigned long long *>(w + 8);
         z->ovf_n = reinterpret_cast<unsigned long long *>(w + 16);
@@ -630,6 +652,9 @@ sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
         z->mstatus = reinterpret_cast<int *>(w + 44);
         z->nnz = reinterpret_cast<unsigned long long *>(w + 48);
         z->dmin = reinterpret_cast<double *>(w + 56);
+        z->tau_w = reinterpret_cast<unsigned long long *>(w + 64);
+        z->mark_w = reinterpret_cast<unsigned long long *>(w + 72);
+        z->lock_w = reinterpret_cast<int *>(w + 80);
     }
     if (e != cudaSuccess) {
         destroy_lz(z);
@@ -675,10 +700,17 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
     SFCI_CUDA(cudaEventRecord(z->ev[0], z->st));
 
     bool last = (i == NL - 1) || (z->p.max_iter > 0 && z->iter + 1 >= z->p.max_iter);
-    // Stream threshold: a quarter of the previous cut; nothing at a cycle's last
-    // vector (u is not formed there); checked below, and redone with 0 if the
-    // N_d largest did not all clear it.
-    double tau = last ? __builtin_inf() : (z->tau_prev > 0.0 ? 0.25 * z->tau_prev : 0.0);
+    // Stream threshold tau: predicted from earlier cuts; nothing at a cycle's
+    // last vector (u is not formed there).  Checked after the truncation and,
+    // if the N_d largest did not all clear it, sigma is redone with the exact
+    // threshold from this attempt's magnitude histogram.
+    double tau = __builtin_inf();
+    if (!last) {
+        // a fraction of the cut at the same basis index one cycle earlier (else of
+        // the previous cut); low on purpose, the merge raises it as it goes
+        const double ci = i < (int)z->cut_at.size() ? z->cut_at[i] : 0.0;
+        tau = (ci > 0.0 ? ci : z->tau_prev) * (i == 0 ? 1.0 / 32.0 : 0.125);
+    }
     std::vector<VecRef> vr(i + 1);
     for (int j = 0; j <= i; ++j) vr[j] = VecRef{z->wr[j], z->wc[j], z->wn[j]};
     for (int attempt = 0;; ++attempt) {
@@ -686,7 +718,7 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
         unsigned long long n_stream = 0, n_live = 0, n_nz = 0;
         double sq = 0.0;
         {
-            const sfci_status rs = bucketed_sigma(z, i, tau, &n_stream, &n_live, &n_nz, &sq);
+            const sfci_status rs = bucketed_sigma(z, i, &tau, &n_stream, &n_live, &n_nz, &sq);
             if (rs != SFCI_OK) return rs;
         }
         info->ms_sigma = z->ms_emit + z->ms_merge;
@@ -773,14 +805,21 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
         const bool complete = tau <= 0.0 || (kept == (unsigned long long)z->nkeep ? !(cut < tau)
                                                                                   : n_nz + wi.n + wm.n <= (unsigned long long)n_items);
         if (!complete) {
-            if (attempt > 0) {
-                set_error("truncation threshold check failed twice");
+            // the predicted threshold hid part of the N_d largest: redo lower
+            // (the merge raises it again as entries stream), last resort 0
+            if (attempt >= 2) {
+                set_error("truncation threshold check failed three times");
                 return SFCI_E_CAPACITY;
             }
-            tau = 0.0;
+            tau = attempt == 0 ? tau / 64.0 : 0.0;
+            info->redo += 1;
             continue;
         }
         z->tau_prev = kept == (unsigned long long)z->nkeep ? cut : 0.0;
+        if ((int)z->cut_at.size() < NL) z->cut_at.assign(NL, 0.0);
+        z->cut_at[i] = z->tau_prev;
+        info->tau = tau;
+        info->cut = z->tau_prev;
         SFCI_CUDA(sort_pairs(z->wr[i + 1], z->wc[i + 1], z->nkeep, z->ndev, key_bits(d.dim),
                              z->scratch + z->off_sort, z->st));
         SFCI_CUDA(normalize_vec(z->wc[i + 1], z->nkeep, z->ndev, z->scratch + z->off_norm, z->st));

@@ -201,6 +201,54 @@ __global__ void uniform_offsets_kernel(unsigned long long *boff, unsigned long l
 // registers (independent loads in flight together), then inserts them; slots
 // taken for the first time are listed, so clearing and streaming out touch only
 // the occupied slots.
+// Called by every thread of the CTA that holds A.lock: the highest histogram
+// bin b whose streamed entries at or above it number >= nkeep (counts read
+// while other CTAs still add, so they only undercount: the threshold is never
+// too high), then tau = max(tau, lower edge of b) and the next mark halfway
+// between out_n and out_cap; releases the lock.
+__device__ __noinline__ void raise_threshold(const MergeArgs &A, int tid, int *s_bin) {
+    constexpr int per = kHistBins / kMT;  // bins per thread, thread 0 owns the top ones
+    __shared__ unsigned long long part[kMT];
+    unsigned long long sum = 0;
+    const int top = kHistBins - 1 - tid * per;
+    for (int q = 0; q < per; ++q) sum += *(volatile unsigned long long *)&A.hist[top - q];
+    part[tid] = sum;
+    __syncthreads();
+    if (tid == 0) {  // exclusive prefix from the top (kMT values)
+        unsigned long long run = 0;
+        for (int t = 0; t < kMT; ++t) {
+            const unsigned long long v = part[t];
+            part[t] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    const unsigned long long need = (unsigned long long)(A.nkeep > 0 ? A.nkeep : 1);
+    unsigned long long run = part[tid];
+    if (run < need && run + sum >= need) {
+        // re-read: counts only grow, so a bin found with fresher counts is still
+        // one with >= nkeep streamed entries at or above it
+        for (int q = 0; q < per; ++q) {
+            run += *(volatile unsigned long long *)&A.hist[top - q];
+            if (run >= need) {
+                *s_bin = top - q;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int b = *s_bin;
+        if (b > 0) atomicMax(A.tau_bits, (unsigned long long)b << kHistShift);
+        const unsigned long long on = *(volatile unsigned long long *)A.out_n;
+        const unsigned long long cap = (unsigned long long)(A.out_cap > 0 ? A.out_cap : 0);
+        *(volatile unsigned long long *)A.mark = on < cap ? on + (cap - on) / 2 : cap;
+        __threadfence();
+        atomicExch(A.lock, 0);
+    }
+    __syncthreads();
+}
+
 template <int kSlots>
 __global__ void __launch_bounds__(kMT)
 merge_kernel(MergeArgs A) {
@@ -210,18 +258,21 @@ merge_kernel(MergeArgs A) {
     unsigned short *occ = reinterpret_cast<unsigned short *>(vals + kSlots);
     unsigned char *flag = reinterpret_cast<unsigned char *>(occ + kSlots);
     __shared__ unsigned cur, n_occ;
+    __shared__ unsigned long long s_tau;
+    __shared__ int s_raise, s_bin;
     const int tid = threadIdx.x, lane = tid & 31;
     const bool screen = A.eps > 0.0;
     // thresholds compared on bit patterns (|x| < t for t >= 0, NaN never below)
-    const unsigned long long eps_bits = abs_bits(A.eps), tau_bits = abs_bits(A.tau);
+    const unsigned long long eps_bits = abs_bits(A.eps);
     for (int sl = tid; sl < kSlots; sl += kMT) keys[sl] = kEmpty, vals[sl] = 0.0, flag[sl] = 0;
-    if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u);
+    if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u), s_tau = *(volatile unsigned long long *)A.tau_bits;
     double sq = 0.0;
     unsigned long long n_live = 0, n_nonzero = 0;
     __syncthreads();
     for (;;) {
         const unsigned bi = cur;  // bucket index within the pass
         if (bi >= A.hi - A.lo) break;
+        const unsigned long long tau_bits = s_tau;
         const unsigned b = A.lo + bi;
         const unsigned cnt = A.count[b];
         const unsigned long long r0 = A.bk.boff[b];
@@ -315,6 +366,7 @@ merge_kernel(MergeArgs A) {
             unsigned long long key = kEmpty;
             double v = 0.0;
             bool live = false, w = false;
+            unsigned hb = 0x80000000u | (unsigned)lane;
             if (t < nocc) {
                 const unsigned sl = occ[t];
                 key = keys[sl];
@@ -328,6 +380,13 @@ merge_kernel(MergeArgs A) {
                 }
                 w = nz && !(ab < tau_bits);
                 keys[sl] = kEmpty, vals[sl] = 0.0, flag[sl] = 0;
+                if (w) hb = (unsigned)(ab >> kHistShift);
+            }
+            // histogram of the streamed entries (lanes sharing a bin add once)
+            if (__any_sync(kFull, w)) {
+                const unsigned peers = __match_any_sync(kFull, hb);
+                if (w && (peers & ((1u << lane) - 1u)) == 0)
+                    atomicAdd(&A.hist[hb], (unsigned long long)__popc(peers));
             }
             n_live += live;
             const unsigned bal = __ballot_sync(kFull, w);
@@ -345,7 +404,16 @@ merge_kernel(MergeArgs A) {
             }
         }
         __syncthreads();
-        if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u);
+        // raise the threshold once the stream passes the mark (one CTA at a time)
+        if (tid == 0) {
+            s_raise = 0;
+            s_bin = -1;
+            const unsigned long long on = *(volatile unsigned long long *)A.out_n;
+            if (on >= *(volatile unsigned long long *)A.mark && atomicCAS(A.lock, 0, 1) == 0) s_raise = 1;
+        }
+        __syncthreads();
+        if (s_raise) raise_threshold(A, tid, &s_bin);
+        if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u), s_tau = *(volatile unsigned long long *)A.tau_bits;
         __syncthreads();
     }
     for (int o = 16; o > 0; o >>= 1) {
