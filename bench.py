@@ -59,6 +59,15 @@ def parse():
                    help="merge-table slots (0 = sized by the solver)")
     p.add_argument("--emit-warps", type=int, default=0,
                    help="warps per CTA of the element generator (0 = 8)")
+    p.add_argument("--workload", default="sfci", choices=["sfci", "scan"],
+                   help="sfci: the 28-orbital solver (headline); scan: 32 uneven instances stepped together")
+    p.add_argument("--scan-cap-scale", type=float, default=1.0,
+                   help="scale factor on the scan instances' vector caps")
+    p.add_argument("--workers", type=int, default=0, help="scan host workers (0 = automatic)")
+    p.add_argument("--tune", action="store_true",
+                   help="scan: pick emit warps, bucket size and workers with the autotuner "
+                        "(on the instances with caps scaled by --tune-cap-scale; cached)")
+    p.add_argument("--tune-cap-scale", type=float, default=0.25)
     p.add_argument("--no-precision", action="store_true",
                    help="skip the float32-element vs float64 comparison")
     p.add_argument("--precision-nkeep", type=int, default=100_000)
@@ -243,6 +252,77 @@ def precision_study(sf, d, nkeep, n_lanczos, steps, stream):
     return out
 
 
+def run_scan(a):
+    """Batched scan: the 32 uneven instances (n 16-24, 5-8 electrons per spin,
+    caps 1e4-2e5, integrals interpolated between two seeded sets) stepped
+    together through sfci_scan, and the same instances one at a time (one
+    worker) for comparison.  value = intermediate elements of all instances
+    per second of wall time (each scan step returns when every instance's step
+    is done on the device)."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2312_01846_gb300 as sf
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    inst_d = gen.batched_scan_instances()
+    systems = [sf.System.from_dict(d) for d in inst_d]
+    caps = [max(1000, int(d["cap"] * a.scan_cap_scale)) for d in inst_d]
+    shape = {"bucket_elems": a.bucket_elems, "emit_warps": a.emit_warps, "workers": a.workers}
+    tuned = None
+    if a.tune:
+        from paper_2312_01846_gb300.tune import tune_scan
+        tcaps = [max(1000, int(c * a.tune_cap_scale)) for c in caps]
+        tuned = tune_scan(systems, tcaps, n_lanczos=a.nlanczos)
+        shape.update(tuned["best"])
+    out = {}
+    for name, workers in (("batched", shape["workers"]), ("one_at_a_time", 1)):
+        inst = [(s_, np.array([0], dtype=np.uint64), np.array([1.0]), c) for s_, c in zip(systems, caps)]
+        sc = sf.Scan(inst, n_lanczos=a.nlanczos, bucket_elems=shape["bucket_elems"],
+                     emit_warps=shape["emit_warps"], workers=workers)
+        for _ in range(a.warmup):
+            sc.step()
+        torch.cuda.synchronize()
+        l0 = sf.kernel_launches()
+        t0 = time.perf_counter()
+        steps = [sc.step() for _ in range(a.steps)]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        el = sum(x["n_elements"] for st in steps for x in st)
+        out[name] = {"value": el / dt, "ms_per_step": 1e3 * dt / a.steps, "elements_per_step": el / a.steps,
+                     "gpu_launches": sf.kernel_launches() - l0,
+                     "lambda_last": [x["lambda_min"] for x in steps[-1]] if steps else None}
+        sc.close()
+        if rank != 0:
+            break
+    hbm, peak_kind = peaks()
+    b = out["batched"]
+    achieved = BYTES_PER_ELEMENT * b["elements_per_step"] / (b["ms_per_step"] * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batched-scan-32-instances-n16to24-caps1e4to2e5x{a.scan_cap_scale:g}",
+                   "instances": len(systems), "caps": caps, "n_lanczos": a.nlanczos,
+                   "parallelism": "single GPU, one stream per instance"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": "whole scan step (wall time)",
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "model": f"{BYTES_PER_ELEMENT} B per connected element"},
+        "gpu_launches": b["gpu_launches"], "cpu_baseline": None, "e2e": None,
+        "detail": out, "speedup_vs_one_at_a_time": (b["value"] / out["one_at_a_time"]["value"]
+                                                    if "one_at_a_time" in out else None),
+        "launch_shape": shape, "autotune": tuned,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for s_ in systems:
+        s_.close()
+    return 0
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -398,6 +478,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "scan":
+        return run_scan(a)
     return run_ours(a)
 
 

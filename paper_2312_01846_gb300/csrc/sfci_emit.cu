@@ -706,7 +706,7 @@ cudaError_t launch_emit_impl(const SysDev &d, const unsigned long long *in_rank,
     if (warps < 1) return cudaErrorInvalidConfiguration;  // one warp's tables exceed shared memory
     const size_t smem = emit_smem_bytes_w(d, warps);
     auto kern = emit_kernel<kMode>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem(kern, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
@@ -743,7 +743,7 @@ cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_ran
                                unsigned long long *weights, cudaStream_t st) {
     if (n_in <= 0) return cudaSuccess;
     const size_t smem = emit_smem_bytes(d, kEmitWarps);
-    cudaError_t e = cudaFuncSetAttribute(row_weight_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem(row_weight_kernel, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, row_weight_kernel, kEmitThreads, smem);

@@ -72,6 +72,25 @@ namespace sfci {
 void count_launch();
 long long launch_count();
 
+// ------------------------------------------------------------- shared memory
+// Let `func` use up to the device's opt-in shared memory per block, less its
+// static shared memory (need: this launch's dynamic bytes, checked against it).  The attribute belongs to the function,
+// not to a launch: setting it to each launch's own size would race between
+// host threads launching one kernel with different sizes, so it is always set
+// to the device maximum.
+template <typename F>
+cudaError_t allow_max_smem(F func, size_t need) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    const int room = optin - (int)fa.sharedSizeBytes;  // opt-in limit less the static shared memory
+    if (room < 0 || need > (size_t)room) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
+}
+
 // ------------------------------------------------------------- error text
 void set_error(const std::string &msg);
 sfci_status cuda_fail(cudaError_t e, const char *what);

@@ -378,16 +378,9 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     bk.boff = static_cast<const unsigned long long *>(z->boff.p);
     const unsigned long long total_cap = z->h_boff[B];
 
-    // streamed-output capacity: with a threshold, a few N_d (from the previous
-    // merge); without, all of sigma (from the previous step or the element count)
-    double sig_need;
-    if (tau > 0.0)
-        sig_need = std::max(16.0 * (double)z->nkeep, 1.5 * (double)z->stream_prev);
-    else if (z->m_prev > 0 && z->nin_prev > 0)
-        sig_need = 1.3 * (double)z->m_prev * std::max(1.0, (double)n_in / (double)z->nin_prev);
-    else
-        sig_need = E;
-    sig_need = std::min(sig_need, E) + 2.0 * (double)z->nkeep + 1024.0;
+    // streamed-output capacity: 16 N_d (the merge raises the threshold to keep
+    // the stream within it) plus room for u's entries on w_i, w_{i-1}
+    double sig_need = std::min(16.0 * (double)z->nkeep, E) + 2.0 * (double)z->nkeep + 1024.0;
     long long ovf_cap = std::max<long long>(1 << 20, z->ovf_cap);
     long long totp = 0;
     for (int j = 0; j <= i; ++j) totp += z->wn[j];

@@ -611,8 +611,7 @@ cudaError_t uniform_offsets(unsigned long long *boff, unsigned long long nb, uns
 template <int kSlots>
 cudaError_t launch_merge_t(const MergeArgs &A, cudaStream_t st) {
     const size_t smem = merge_smem(kSlots);
-    cudaError_t e = cudaFuncSetAttribute(merge_kernel<kSlots>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = allow_max_smem(merge_kernel<kSlots>, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, merge_kernel<kSlots>, kMT, smem);

@@ -294,7 +294,7 @@ sfci_status sfci_rdm12(const sfci_system *s, const uint64_t *rank, const double 
     norm2_finish<<<1, 32, 0, st>>>(partial, kNormBlocks, nrm);
     if (n > 0) {
         const size_t smem = rdm_block_smem(d) + kWarps * rdm_warp_smem(d);
-        SFCI_CUDA(cudaFuncSetAttribute(rdm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SFCI_CUDA(allow_max_smem(rdm_kernel, smem));
         int per_sm = 0;
         SFCI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rdm_kernel, kThreads, smem));
         if (per_sm < 1) {
