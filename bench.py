@@ -68,6 +68,9 @@ def parse():
                    help="scan: pick emit warps, bucket size and workers with the autotuner "
                         "(on the instances with caps scaled by --tune-cap-scale; cached)")
     p.add_argument("--tune-cap-scale", type=float, default=0.25)
+    p.add_argument("--no-screen", action="store_true",
+                   help="skip the heat-bath style selection study (eps_element)")
+    p.add_argument("--screen-eps", default="1e-6,1e-5,1e-4")
     p.add_argument("--no-precision", action="store_true",
                    help="skip the float32-element vs float64 comparison")
     p.add_argument("--precision-nkeep", type=int, default=100_000)
@@ -86,6 +89,18 @@ def config(a, extra=None):
     if extra:
         c.update(extra)
     return c
+
+
+def reduce_over_ranks(ms, elements, dist=None, device="cuda"):
+    """Whole-job timing of replicas: the slowest rank's time and the elements
+    of all ranks (each rank runs the full workload: weak scaling)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    e = torch.tensor([float(elements)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
 
 
 def dist_env():
@@ -323,6 +338,40 @@ def run_scan(a):
     return 0
 
 
+def screen_study(sf, d, nkeep, n_lanczos, steps, stream, eps_list):
+    """The solver with the heat-bath style selection (eps_element) against the
+    exact sigma: throughput (enumerated elements per second, so a faster step
+    shows as a higher rate) and the energy difference at every cycle end."""
+    import numpy as np
+    import torch
+    gsys = sf.System.from_dict(d)
+    out = {"workload": f"sfci-28o-7a7b-L200-clustered-Nd{nkeep:.0e}-NL{n_lanczos}".replace("+0", "") +
+                       f", {steps} steps from the aufbau determinant", "runs": []}
+    for eps in [0.0] + list(eps_list):
+        lz = sf.Lanczos(gsys, np.array([0], dtype=np.uint64), np.array([1.0]), nkeep, n_lanczos,
+                        stream=stream, eps_element=eps)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        infos = [lz.step() for _ in range(steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        lz.close()
+        out["runs"].append({"eps_element": eps,
+                            "elements_per_s": sum(i["n_elements"] for i in infos) / (ms * 1e-3),
+                            "ms_per_step": ms / steps,
+                            "ms_sigma_mean": statistics.mean(i["ms_sigma"] for i in infos),
+                            "lambda": [i["lambda_min"] for i in infos if i["cycle_end"]]})
+    exact = out["runs"][0]
+    for r in out["runs"][1:]:
+        r["delta_e_hartree"] = [b - a for a, b in zip(exact["lambda"], r["lambda"])]
+        r["speedup"] = r["elements_per_s"] / exact["elements_per_s"]
+    gsys.close()
+    return out
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -371,13 +420,7 @@ def run_ours(a):
     launches = sf.kernel_launches() - launches0
     ms = ev0.elapsed_time(ev1)
     elements = sum(i["n_elements"] for i in infos)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    e = torch.tensor([float(elements)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    elements_all = float(e.item())
+    ms_max, elements_all = reduce_over_ranks(ms, elements, dist, "cuda")
     value = elements_all / (ms_max * 1e-3)
     steps_per_s = a.steps / (ms_max * 1e-3)
 
@@ -448,6 +491,11 @@ def run_ours(a):
     if rank == 0 and not a.no_precision:
         precision = precision_study(sf, d, a.precision_nkeep, a.nlanczos, a.precision_steps, stream)
 
+    screen = None
+    if rank == 0 and not a.no_screen:
+        screen = screen_study(sf, d, a.precision_nkeep, a.nlanczos, 20, stream,
+                              [float(x) for x in a.screen_eps.split(",") if x])
+
     last_lambda = [i["lambda_min"] for i in infos if i["cycle_end"]]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -460,6 +508,7 @@ def run_ours(a):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),
         "precision": precision,
+        "heat_bath_screen": screen,
         "detail": {"n_in": infos[-1]["n_in"], "n_sigma": infos[-1]["n_sigma"],
                    "elements_per_step": el_per_launch, "lambda_min": last_lambda[-1] if last_lambda else None,
                    "ms_sigma_mean": ms_sig,

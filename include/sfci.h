@@ -186,6 +186,10 @@ typedef struct sfci_params {
                                0 = 85 % of what is free (one solver per device)   */
     int32_t emit_warps;     /* warps per CTA of the element generator (1..8); 0 = 8 */
     int32_t reserved;       /* pass 0                                                */
+    double eps_element;     /* heat-bath style selection (the outlook of Sec. 4):
+                               intermediate elements with |<D'|H|D> c_D| <
+                               eps_element are not generated, whole excitation
+                               classes skipped by integral bounds; 0 = exact sigma */
 } sfci_params;
 
 typedef struct sfci_step_info {

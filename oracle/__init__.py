@@ -82,7 +82,7 @@ def lib():
         L.or_connected.argtypes = [C.c_int, C.c_uint64, C.c_uint64, _u64p, _u64p]
         L.or_sigma.restype = C.c_int64
         L.or_sigma.argtypes = [C.POINTER(_Sys), _u64p, _f64p, C.c_int64, _u64p, _f64p,
-                               _f64p, C.c_int64, _i64p, C.c_int]
+                               _f64p, C.c_int64, _i64p, C.c_int, C.c_double]
         L.or_sigma_entries.restype = None
         L.or_sigma_entries.argtypes = [C.POINTER(_Sys), _u64p, _f64p, C.c_int64, _u64p,
                                        C.c_int64, _f64p, _f64p, _i32p, C.c_int]
@@ -214,9 +214,11 @@ def fci_ground_energy(sys: System):
 
 # ---------------------------------------------------------------- sigma
 
-def sigma(sys: System, rank, coef, threads=None):
+def sigma(sys: System, rank, coef, threads=None, eps_element=0.0):
     """sigma = H psi by list-sort-merge.  Returns (rank, value, abs_sum,
-    n_elements) with ranks ascending; abs_sum[k] = sum_D |<k|H|D> c_D|."""
+    n_elements) with ranks ascending; abs_sum[k] = sum_D |<k|H|D> c_D|.
+    eps_element > 0: intermediate elements with |<k|H|D> c_D| < eps_element are
+    not generated (heat-bath style selection, Sec. 4 outlook)."""
     r = np.ascontiguousarray(rank, dtype=np.uint64)
     c = np.ascontiguousarray(coef, dtype=np.float64)
     nt = threads or n_threads()
@@ -227,7 +229,8 @@ def sigma(sys: System, rank, coef, threads=None):
         oabs = np.empty(cap)
         nel = C.c_int64(0)
         m = lib().or_sigma(sys.ref, _p(r, _u64p), _p(c, _f64p), r.size, _p(orank, _u64p),
-                           _p(oval, _f64p), _p(oabs, _f64p), cap, C.byref(nel), nt)
+                           _p(oval, _f64p), _p(oabs, _f64p), cap, C.byref(nel), nt,
+                           float(eps_element))
         if m < 0:
             raise MemoryError("oracle sigma: out of memory")
         if m <= cap:
@@ -323,7 +326,7 @@ def gen_eig_lowest(T, S, drop=1e-12):
 
 
 def sfci(sys: System, init_rank, init_coef, n_keep, n_lanczos=10, n_iter=30,
-         eps_screen=0.0, conv_tol=None, threads=None, record_vectors=False):
+         eps_screen=0.0, conv_tol=None, threads=None, record_vectors=False, eps_element=0.0):
     """The truncated Lanczos of Sec. 2.1.
 
     Each cycle starts from w_0 (truncated, normalised) and for i = 0..N_L-1:
@@ -346,7 +349,7 @@ def sfci(sys: System, init_rank, init_coef, n_keep, n_lanczos=10, n_iter=30,
         T = np.zeros((NL, NL))
         Sm = np.zeros((NL, NL))
         for i in range(NL):
-            sr, sv, _, nel = sigma(sys, W[i][0], W[i][1], threads)
+            sr, sv, _, nel = sigma(sys, W[i][0], W[i][1], threads, eps_element)
             sr, sv = screen(sr, sv, eps_screen)
             it += 1
             for j in range(i + 1):

@@ -394,7 +394,10 @@ static int cmp_elem(const void *x, const void *y)
 
 /* sigma = H psi (Sec. 2.2).  Step 1: every input entry (D, c_D) generates its
  * intermediate elements (rank(D'), <D'|H|D> c_D) for D' = D and every D'
- * connected to D; products that are exactly zero are not generated.  Step 2:
+ * connected to D; products that are exactly zero are not generated, nor, with
+ * eps_elem > 0, products with |<D'|H|D> c_D| < eps_elem (the heat-bath style
+ * selection the outlook of Sec. 4 proposes; eps_elem = 0 is the exact sigma).
+ * Step 2:
  * the elements are sorted by (target, source) and each target's run is summed
  * in ascending source order.  out_abs receives sum |element| per target.
  * Returns the number of distinct targets (entries beyond cap are not
@@ -402,7 +405,7 @@ static int cmp_elem(const void *x, const void *y)
  * connected elements enumerated (diagonal included). */
 int64_t or_sigma(const or_sys *S, const uint64_t *in_rank, const double *in_coef,
                  int64_t n_in, uint64_t *out_rank, double *out_val, double *out_abs,
-                 int64_t cap, int64_t *n_elements, int n_threads)
+                 int64_t cap, int64_t *n_elements, int n_threads, double eps_elem)
 {
     int n = S->n, na = S->na, nb = S->nb;
     int64_t per = or_n_connected(n, na, nb) + 1;
@@ -426,7 +429,7 @@ int64_t or_sigma(const or_sys *S, const uint64_t *in_rank, const double *in_coef
             for (int64_t e = 0; e < m; e++) {
                 double v = or_hmat(S, a, b, ta[e], tb[e]) * in_coef[s];
                 or_elem *o = &el[s * per + e];
-                o->tgt = (v != 0.0) ? or_det_rank(n, nb, ta[e], tb[e]) : UINT64_MAX;
+                o->tgt = (v != 0.0 && !(fabs(v) < eps_elem)) ? or_det_rank(n, nb, ta[e], tb[e]) : UINT64_MAX;
                 o->src = s;
                 o->v = v;
             }

@@ -34,7 +34,8 @@ class Params(C.Structure):
                 ("eps_screen", C.c_double), ("conv_tol", C.c_double),
                 ("n_lanczos", C.c_int32), ("max_iter", C.c_int32),
                 ("flags", C.c_uint32), ("bucket_elems", C.c_int32),
-                ("mem_budget", C.c_int64), ("emit_warps", C.c_int32), ("reserved", C.c_int32)]
+                ("mem_budget", C.c_int64), ("emit_warps", C.c_int32), ("reserved", C.c_int32),
+                ("eps_element", C.c_double)]
 
 
 class StepInfo(C.Structure):
@@ -322,13 +323,13 @@ class Lanczos:
 
     def __init__(self, sys: System, init_rank, init_coef, n_keep, n_lanczos=10, max_iter=0,
                  eps_screen=0.0, conv_tol=0.0, table_capacity=0, bucket_elems=0, stream=None,
-                 mem_budget=0, emit_warps=0):
+                 mem_budget=0, emit_warps=0, eps_element=0.0):
         self.sys = sys
         r = _dev(init_rank, torch.int64)
         c = _dev(init_coef, torch.float64)
         self.params = Params(int(n_keep), int(table_capacity), float(eps_screen), float(conv_tol),
                              int(n_lanczos), int(max_iter), 0, int(bucket_elems),
-                             int(mem_budget), int(emit_warps), 0)
+                             int(mem_budget), int(emit_warps), 0, float(eps_element))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         _check(lib().sfci_lanczos_create(C.byref(h), sys.handle, C.byref(self.params), _ptr(r),
@@ -385,13 +386,13 @@ class Scan:
     instances: list of (System, init_rank, init_coef, n_keep) tuples."""
 
     def __init__(self, instances, n_lanczos=10, max_iter=0, eps_screen=0.0, bucket_elems=0,
-                 emit_warps=0, workers=0):
+                 emit_warps=0, workers=0, eps_element=0.0):
         k = len(instances)
         self.systems = [inst[0] for inst in instances]
         self._vecs = [(_dev(inst[1], torch.int64), _dev(inst[2], torch.float64)) for inst in instances]
         self.params = (Params * k)(*[
             Params(int(inst[3]), 0, float(eps_screen), 0.0, int(n_lanczos), int(max_iter), 0,
-                   int(bucket_elems), 0, int(emit_warps), 0) for inst in instances])
+                   int(bucket_elems), 0, int(emit_warps), 0, float(eps_element)) for inst in instances])
         torch.cuda.synchronize()
         sysh = (_vp * k)(*[s.handle.value for s in self.systems])
         rk = (_vp * k)(*[r.data_ptr() for r, _ in self._vecs])

@@ -1,6 +1,8 @@
 // C ABI of libsfci.so: systems, Eq. 12 rank/unrank, sigma = H psi, the Eq. 11
 // truncation and the element export.  Declarations and contracts: sfci.h.
+#include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -180,6 +182,32 @@ sfci_status sfci_system_create(sfci_system **out, int n, int na, int nb, const d
     o = a256(o + bt.size() * 8);
     const size_t off_p = o;
     o = a256(o + pairs.size());
+    // bounds for the heat-bath style screen (times 1 + 1e-6: float32 elements
+    // may exceed the float64 values by a few units in the last place)
+    std::vector<double> bab(nh, 0.0), bss(nh, 0.0);
+    for (int a = 0; a < n; ++a)
+        for (int i = 0; i < n; ++i) {
+            // opposite-spin double with alpha hop i -> a: |(ai|bj)|, max over (b, j)
+            double m = 0.0;
+            for (size_t t = 0; t < nh; ++t) m = std::max(m, std::fabs(g_host[(size_t(a) * n + i) * nh + t]));
+            bab[size_t(a) * n + i] = m * (1.0 + 1e-6);
+        }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            // same-spin double (i, j) -> (a, b): |(ai|bj) - (aj|bi)|, max over (a, b)
+            double m = 0.0;
+            for (int a = 0; a < n; ++a)
+                for (int b = 0; b < n; ++b) {
+                    const double x = g_host[((size_t(a) * n + i) * n + b) * n + j];
+                    const double y = g_host[((size_t(a) * n + j) * n + b) * n + i];
+                    m = std::max(m, std::fabs(x - y));
+                }
+            bss[size_t(i) * n + j] = m * (1.0 + 1e-6);
+        }
+    const size_t off_bab = o;
+    o = a256(o + nh * 8);
+    const size_t off_bss = o;
+    o = a256(o + nh * 8);
     const size_t off_hf = o;
     if (fp32) o = a256(o + nh * 4);
     const size_t off_gf = o;
@@ -208,6 +236,8 @@ sfci_status sfci_system_create(sfci_system **out, int n, int na, int nb, const d
     if (e == cudaSuccess) e = cudaMemcpy(blk + off_g, g_host, ng * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(blk + off_bt, bt.data(), bt.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(blk + off_p, pairs.data(), pairs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(blk + off_bab, bab.data(), nh * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(blk + off_bss, bss.data(), nh * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && fp32) e = cudaMemcpy(blk + off_hf, hf.data(), nh * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && fp32) e = cudaMemcpy(blk + off_gf, gf.data(), ng * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -222,6 +252,8 @@ sfci_status sfci_system_create(sfci_system **out, int n, int na, int nb, const d
     d.pairs = reinterpret_cast<const unsigned char *>(blk + off_p);
     d.hf = fp32 ? reinterpret_cast<const float *>(blk + off_hf) : nullptr;
     d.gf = fp32 ? reinterpret_cast<const float *>(blk + off_gf) : nullptr;
+    d.bound_ab = reinterpret_cast<const double *>(blk + off_bab);
+    d.bound_ss = reinterpret_cast<const double *>(blk + off_bss);
     s->d = d;
     s->dev_block = blk;
     *out = s;

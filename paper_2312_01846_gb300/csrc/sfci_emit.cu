@@ -306,7 +306,7 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
             if (!want[k]) continue;
             v[k] = __dmul_rn(e[k], c);
             tg[k] = ha[k] * cb + hb[k];
-            ok[k] = nonzero(v[k]);
+            ok[k] = nonzero(v[k]) && !(fabs(v[k]) < o.b.eps_elem);
         }
         if (single >= 0) single_append(o.b, (unsigned)single, ok, tg, v);
         else warp_append(o.b, ok, bk, tg, v);
@@ -427,6 +427,11 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     const RowCtx rc = row_ctx(o.b, rankA1[x]);
                     keep = ctx_in_pass(o.b, rc);
                     rcv = (unsigned long long)rc.first << 32 | rc.ns;
+                    // heat-bath style screen: no beta hop can lift |(ai|bj) c| to eps
+                    if (keep && o.b.eps_elem > 0.0) {
+                        const int io = x / d.va, iv = x - io * d.va;
+                        keep = !(fabs(c) * __ldg(&d.bound_ab[virA[iv] * n + occA[io]]) < o.b.eps_elem);
+                    }
                 } else {
                     keep = true;
                 }
@@ -512,6 +517,9 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             for (int p = 0; p < npo; ++p) {
                 const int io = po[2 * p], jo = po[2 * p + 1];
                 const int i = occ[io], j = occ[jo];
+                if (kMode == kModeBucket && o.b.eps_elem > 0.0 &&
+                    fabs(c) * __ldg(&d.bound_ss[i * n + j]) < o.b.eps_elem)
+                    continue;  // heat-bath style screen: no (a, b) of this pair survives
                 const unsigned long long rem = str ^ (1ull << i) ^ (1ull << j);
                 pair_prefix(occ, M, io, jo, bt, ks, pre);
                 for (int q0 = 0; q0 < npv; q0 += 32 * kU) {
@@ -586,7 +594,8 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
 // gets the single plus one element per beta hop; each alpha-alpha double's row
 // gets one element.  One warp per input determinant.
 __global__ void __launch_bounds__(kEmitThreads)
-row_weight_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank, long long n_in,
+row_weight_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
+                  const double *__restrict__ in_coef, long long n_in, double eps,
                   unsigned long long *__restrict__ weights) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int n = d.n, ks = d.ks;
@@ -606,19 +615,35 @@ row_weight_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank
     const unsigned long long w_single = 1ull + d.sb;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned char *pOB = pairs + 2 * d.pair_off[2];
     for (long long s = gw; s < n_in; s += nw) {
         const unsigned long long r = in_rank[s];
         const unsigned long long hA = r / cb;
         const unsigned long long alpha = string_unrank_warp(hA, n, d.na, bt, ks);
-        build_lists(alpha, 0ull, n, occA, virA, occB, virB);
+        const double ac = eps > 0.0 ? fabs(in_coef[s]) : 0.0;
+        unsigned long long beta = 0;
+        if (eps > 0.0) beta = string_unrank_warp(r - hA * cb, n, d.nb, bt, ks);
+        build_lists(alpha, beta, n, occA, virA, occB, virB);
         __syncwarp();
-        if (lane == 0) atomicAdd(&weights[hA], w_self);
+        if (lane == 0) {
+            unsigned long long w = w_self;
+            if (eps > 0.0) {  // beta-beta pairs the screen removes
+                w = 1ull + d.sb;
+                for (int p = 0; p < d.po_b; ++p)
+                    if (!(ac * __ldg(&d.bound_ss[occB[pOB[2 * p]] * n + occB[pOB[2 * p + 1]]]) < eps))
+                        w += (unsigned long long)d.pv_b;
+            }
+            atomicAdd(&weights[hA], w);
+        }
         for (int x = lane; x < d.sa; x += 32) {
             const int io = x / d.va, iv = x - io * d.va;
-            atomicAdd(&weights[string_rank(alpha ^ (1ull << occA[io]) ^ (1ull << virA[iv]), bt, ks)], w_single);
+            const bool hops = !(eps > 0.0 && ac * __ldg(&d.bound_ab[virA[iv] * n + occA[io]]) < eps);
+            atomicAdd(&weights[string_rank(alpha ^ (1ull << occA[io]) ^ (1ull << virA[iv]), bt, ks)],
+                      hops ? w_single : 1ull);
         }
         for (int p = 0; p < d.po_a; ++p) {
             const int io = pOA[2 * p], jo = pOA[2 * p + 1];
+            if (eps > 0.0 && ac * __ldg(&d.bound_ss[occA[io] * n + occA[jo]]) < eps) continue;
             const unsigned long long rem = alpha ^ (1ull << occA[io]) ^ (1ull << occA[jo]);
             pair_prefix(occA, d.na, io, jo, bt, ks, pre);
             for (int q = lane; q < d.pv_a; q += 32)
@@ -739,7 +764,8 @@ cudaError_t launch_emit_buckets(const SysDev &d, const unsigned long long *in_ra
     return launch_emit_impl<kModeBucket>(d, in_rank, in_coef, n_in, o, st, warps);
 }
 
-cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_rank, long long n_in,
+cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_rank,
+                               const double *in_coef, long long n_in, double eps_elem,
                                unsigned long long *weights, cudaStream_t st) {
     if (n_in <= 0) return cudaSuccess;
     const size_t smem = emit_smem_bytes(d, kEmitWarps);
@@ -753,7 +779,7 @@ cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_ran
     long long grid = (long long)device_sms() * per_sm;
     if (want < grid) grid = want;
     count_launch();
-    row_weight_kernel<<<(unsigned)grid, kEmitThreads, smem, st>>>(d, in_rank, n_in, weights);
+    row_weight_kernel<<<(unsigned)grid, kEmitThreads, smem, st>>>(d, in_rank, in_coef, n_in, eps_elem, weights);
     return cudaGetLastError();
 }
 

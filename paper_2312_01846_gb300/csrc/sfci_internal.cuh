@@ -54,6 +54,10 @@ struct SysDev {
     const unsigned char *pairs;       // 2 bytes per pair: (first, second) positions, first < second
     const float *hf;     // float32 copies of h and g (SFCI_FP32_ELEMENTS), else null
     const float *gf;
+    // element bounds for the heat-bath style screen: bound_ab[a*n+i] >= |(ai|bj)|
+    // for every (b, j); bound_ss[i*n+j] >= |(ai|bj) - (aj|bi)| for every (a, b)
+    const double *bound_ab;
+    const double *bound_ss;
 };
 
 }  // namespace sfci
@@ -239,6 +243,7 @@ struct BucketOut {
     unsigned *count;          // [B] elements that arrived per bucket
     Slot *elem;               // regions of buckets [lo, hi), relative to boff[lo]
     unsigned long long base;  // boff[lo]
+    double eps_elem;          // elements with |<D'|H|D> c_D| < eps_elem are not generated (0: off)
     Slot *ovf;                // [ovf_cap]
     unsigned long long *ovf_n;
     long long ovf_cap;
@@ -291,7 +296,8 @@ cudaError_t launch_emit_buckets(const SysDev &d, const unsigned long long *in_ra
                                 cudaStream_t st, int warps = 0);
 // weights[ha] += intermediate elements bound for alpha string ha (enumerated,
 // zeros included), over all input determinants
-cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_rank, long long n_in,
+cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_rank,
+                               const double *in_coef, long long n_in, double eps_elem,
                                unsigned long long *weights, cudaStream_t st);
 cudaError_t launch_debug_excitations(const SysDev &d, const unsigned long long *in_rank,
                                      long long n_in, long long *src, unsigned long long *tgt,

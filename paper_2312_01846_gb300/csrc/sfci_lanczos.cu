@@ -322,7 +322,8 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if ((r = ensure(z->weights, nrows * 8, z->st, "row weights", 1.5))) return r;
         if ((r = ensure(z->rowmap, nrows * 8, z->st, "row map", 1.5))) return r;
         SFCI_CUDA(cudaMemsetAsync(z->weights.p, 0, nrows * 8, z->st));
-        SFCI_CUDA(launch_row_weights(d, z->wr[i], n_in, static_cast<unsigned long long *>(z->weights.p), z->st));
+        SFCI_CUDA(launch_row_weights(d, z->wr[i], z->wc[i], n_in, z->p.eps_element,
+                                     static_cast<unsigned long long *>(z->weights.p), z->st));
         z->h_weights.resize(nrows);
         SFCI_CUDA(cudaMemcpyAsync(z->h_weights.data(), z->weights.p, nrows * 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaStreamSynchronize(z->st));
@@ -469,6 +470,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             bo.count = P<unsigned>(z->bcount);
             bo.elem = P<Slot>(z->belem);
             bo.base = z->h_boff[lo];
+            bo.eps_elem = z->p.eps_element > 0.0 ? z->p.eps_element : 0.0;
             bo.ovf = P<Slot>(z->bovf);
             bo.ovf_n = z->ovf_n;
             bo.ovf_cap = z->ovf_cap;
@@ -600,8 +602,8 @@ sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
         return SFCI_E_INVALID;
     }
     if (params->emit_warps < 0 || params->emit_warps > 8 || params->mem_budget < 0 ||
-        params->bucket_elems < 0) {
-        set_error("need 0 <= emit_warps <= 8, mem_budget >= 0 and bucket_elems >= 0");
+        params->bucket_elems < 0 || !(params->eps_element >= 0.0)) {
+        set_error("need 0 <= emit_warps <= 8, mem_budget, bucket_elems, eps_element >= 0");
         return SFCI_E_INVALID;
     }
     sfci_lanczos *z = new (std::nothrow) sfci_lanczos();

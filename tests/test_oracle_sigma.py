@@ -31,6 +31,29 @@ def test_sigma_equals_dense_product(orc):
     assert np.all(np.abs(sv) <= sa * (1 + 1e-15))
 
 
+def test_sigma_element_screen_against_dense(orc):
+    """Heat-bath style selection (Sec. 4 outlook): with eps_element the
+    products |H_kD c_D| < eps are not generated.  Against the dense H: sigma_k
+    = sum over the kept products, support = rows with a kept product; eps = 0
+    is the exact sigma."""
+    S = _cfg0(orc)
+    H = orc.dense_h(S)
+    rng = np.random.default_rng(2)
+    r = np.sort(rng.choice(4900, size=600, replace=False)).astype(np.uint64)
+    c = rng.normal(size=r.size) * np.exp(rng.uniform(-8, 0, size=r.size))
+    P = H[:, r.astype(np.int64)] * c  # every product H_kD c_D
+    for eps in (0.0, 1e-4, 1e-2):
+        keep = (P != 0.0) & ~(np.abs(P) < eps)
+        want = np.where(keep, P, 0.0).sum(axis=1)
+        absw = np.where(keep, np.abs(P), 0.0).sum(axis=1)
+        support = np.nonzero(keep.any(axis=1))[0]
+        sr, sv, sa, _ = orc.sigma(S, r, c, eps_element=eps)
+        assert np.array_equal(sr.astype(np.int64), support)
+        assert np.all(np.abs(sv - want[support]) <= 1e-13 * absw[support])
+        if eps > 0:  # the screen removed products
+            assert 0 < np.count_nonzero(keep) < np.count_nonzero(P)
+
+
 def test_sigma_pull_equals_push_bitwise(orc):
     """Each pulled entry sums the same products in the same order as the
     list-sort-merge, so the two agree bit for bit."""
