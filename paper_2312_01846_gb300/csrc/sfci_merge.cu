@@ -36,11 +36,18 @@ namespace {
 constexpr int kMT = SFCI_MERGE_THREADS;  // merge CTA threads
 constexpr int kPre = 8;              // elements each thread loads before inserting
 
-// slot in the shared-memory table: hash bits below those that chose the
-// bucket (hash mode); row mode uses the top bits
+// slot in the shared-memory table.  Hash mode: the mix64 bits just below
+// those that chose the bucket.  Row mode: a split row's bucket was chosen by
+// the top bits of mix64 of the beta index, so the keys of one bucket share
+// those bits; the slot comes from an independent mix (xor-shift-multiply
+// finaliser) instead, or the keys would crowd a few slots.
 template <int kSlots>
 __device__ __forceinline__ unsigned smem_slot(unsigned long long key, int log2B) {
-    return (unsigned)(mix64(key) >> (64 - log2B - 13)) & (kSlots - 1);
+    if (log2B > 0) return (unsigned)(mix64(key) >> (64 - log2B - 13)) & (kSlots - 1);
+    key ^= key >> 31;
+    key *= 0xD6E8FEB86659FD93ull;
+    key ^= key >> 32;
+    return (unsigned)key & (kSlots - 1);
 }
 
 __device__ __forceinline__ unsigned long long abs_bits(double v) {

@@ -1,0 +1,89 @@
+"""Full-size parity of one Lanczos step on the 28-orbital workload (N_d = 1e5
+and the benchmark's 1e6), in the launch configuration bench.py times, checked
+on sampled entries the oracle computes one by one.
+
+After a step i the solver holds w_{i+1} = normalise(top_{N_d}(u)) with
+u = sigma_i - a w_i - b w_{i-1} (Eqs. 10-11).  For sampled ranks k:
+  - kept k: w_{i+1}[k] = u_k / ||top(u)||, so w_{i+1}[k] / u_k is one common
+    factor (u_k from the oracle's pulled sigma_k and the step's a, b);
+  - k in sigma's support but not kept: |u_k| <= the smallest kept |u| (ties
+    go to the smaller rank, so equality is allowed).
+Bars: the ratio within 1e-10 relative; the cut within 1e-10 relative.
+"""
+import numpy as np
+import pytest
+
+import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2312_01846_gb300 as sf
+    sf.lib()
+    return sf
+
+
+def _vec(sf, lz):
+    r, c = lz.vector()
+    return sf.to_u64(r), c.cpu().numpy()
+
+
+def _lookup(r, c, keys):
+    pos = np.searchsorted(r, keys)
+    pos = np.minimum(pos, r.size - 1)
+    hit = r[pos] == keys
+    return np.where(hit, c[pos], 0.0), hit
+
+
+@pytest.mark.parametrize("n_keep,steps", [(100_000, 5), (1_000_000, 4)])
+def test_step_sampled_against_oracle(sf, orc, n_keep, steps):
+    d = gen.config_system(2)
+    n, na, nb = d["n"], d["na"], d["nb"]
+    gsys, osys = sf.System.from_dict(d), orc.System.from_dict(d)
+    lz = sf.Lanczos(gsys, np.array([0], dtype=np.uint64), np.array([1.0]), n_keep, 10)
+    vecs = [_vec(sf, lz)]
+    infos = []
+    for _ in range(steps):
+        infos.append(lz.step())
+        vecs.append(_vec(sf, lz))
+    lz.close()
+    i = steps - 1
+    info = infos[i]
+    assert not info["cycle_end"] and info["n_kept"] == n_keep and info["n_in"] == n_keep
+    (ri, ci), (rm, cm), (ro, co) = vecs[i], vecs[i - 1], vecs[i + 1]
+    a, b = info["a"], info["b"]
+    rng = np.random.default_rng(7)
+
+    def u_of(keys):
+        s, _, _ = orc.sigma_entries(osys, ri, ci, keys)
+        wi, _ = _lookup(ri, ci, keys)
+        wm, _ = _lookup(rm, cm, keys)
+        return s - a * wi - b * wm
+
+    # kept entries: one common scale
+    kk = np.sort(rng.choice(ro, size=300, replace=False))
+    wk, _ = _lookup(ro, co, kk)
+    uk = u_of(kk)
+    ratio = wk / uk
+    scale = np.median(ratio)
+    assert np.all(np.abs(ratio / scale - 1.0) < 1e-10), np.max(np.abs(ratio / scale - 1.0))
+    cut = np.min(np.abs(co)) / abs(scale)  # smallest kept |u|
+    # entries of sigma's support that were not kept: connected to sampled sources
+    src = rng.choice(ri.size, size=40, replace=False)
+    sa, sb = orc.det_unrank(n, na, nb, ri[src])
+    cand = []
+    for x, y in zip(sa, sb):
+        ca, cb_ = orc.connected(n, na, nb, x, y)
+        cand.append(orc.det_rank(n, nb, ca[::97], cb_[::97]))
+    cand = np.unique(np.concatenate(cand))
+    _, kept = _lookup(ro, co, cand)
+    out = cand[~kept]
+    uo = u_of(out)
+    print(f"N_d={n_keep}: step {i}, cut {cut:.4g}, {out.size} unkept samples, "
+          f"max |u| there {np.max(np.abs(uo)):.4g}, tau {info['tau']:.4g}, redo {info['redo']}")
+    assert np.all(np.abs(uo) <= cut * (1 + 1e-10))

@@ -60,10 +60,19 @@ def test_scan_untruncated_matches_single_and_oracle(sf, orc):
 
 
 def test_scan_truncated_uneven_instances(sf):
-    """Three instances of the batched-scan generator (uneven n, electrons and
-    N_d, interpolated integrals) with reduced caps: scan vs one at a time."""
-    inst_d = gen.batched_scan_instances()
-    pick = [inst_d[2], inst_d[12], inst_d[29]]
+    """Three uneven instances with reduced caps, integrals interpolated between
+    two seeded sets as in the batched-scan generator, scan vs one at a time.
+    n_alpha != n_beta: with equal counts, spin-flip partners have exactly equal
+    |c|, and which partner survives a cut at such a tie depends on rounding, so
+    truncated runs could not be compared entry for entry."""
+    A = gen.molecular_integrals(12, 16, seed=31)
+    Bs = gen.molecular_integrals(12, 16, seed=32)
+    pick = []
+    for (n, na, nb, lam) in [(10, 4, 3, 0.0), (12, 5, 4, 0.5), (9, 3, 2, 1.0)]:
+        h = (1 - lam) * A["h"] + lam * Bs["h"]
+        g = (1 - lam) * A["g"] + lam * Bs["g"]
+        pick.append(dict(h=np.ascontiguousarray(h[:n, :n]), g=np.ascontiguousarray(g[:n, :n, :n, :n]),
+                         e_core=0.0, n=n, na=na, nb=nb))
     caps = [3000, 1500, 2500]
     systems = [sf.System.from_dict(d) for d in pick]
     n_iter = 20
@@ -79,7 +88,7 @@ def test_scan_truncated_uneven_instances(sf):
         lam_one = _lams([lz.step() for _ in range(n_iter)])
         lz.close()
         lam_scan = _lams(infos_scan)
-        print(f"instance {k}: n={pick[k]['n']} ne={pick[k]['na']} cap={caps[k]} "
+        print(f"instance {k}: n={pick[k]['n']} {pick[k]['na']}a{pick[k]['nb']}b cap={caps[k]} "
               f"scan-single {np.array(lam_scan) - np.array(lam_one)}")
         assert np.max(np.abs(np.array(lam_scan) - np.array(lam_one))) < 1e-8
         r, c = vec[k]
