@@ -403,7 +403,8 @@ def run_ours(a):
                     emit_warps=a.emit_warps)
     def brief(i):
         return {k: i[k] for k in ("n_in", "n_sigma", "n_passes", "ms_plan", "ms_emit", "ms_merge",
-                                  "ms_topk", "ms_step", "redo", "tau", "cut")}
+                                  "ms_topk", "ms_step", "redo", "tau", "cut", "pass_budget_gb",
+                                  "regions_gb")}
 
     warm = []
     for _ in range(a.warmup):

@@ -222,6 +222,8 @@ typedef struct sfci_step_info {
     double cut;        /* |coef| of the N_d-th kept entry of u (0 if fewer kept)    */
     int32_t redo;      /* sigma recomputed because tau hid part of the N_d largest  */
     int32_t reserved;
+    double pass_budget_gb; /* device memory one pass's element regions may use (GB) */
+    double regions_gb;     /* element regions of all buckets (GB): passes ~ this/budget */
 } sfci_step_info;
 
 typedef struct sfci_lanczos sfci_lanczos; /* opaque; owns w_0..w_{N_L-1}, T, S, table */

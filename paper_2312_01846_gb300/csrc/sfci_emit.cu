@@ -35,10 +35,10 @@ __host__ __device__ inline size_t block_smem(const SysDev &d) {
     return align16(size_t(d.n + 1) * d.ks * 8) + align16(size_t(d.n_pairs) * 2);
 }
 
-// per warp: rankA1, rankB1 (u64), prefix sums (192 u64), hopRC (u64 per alpha
+// per warp: rankA1, rankB1 (u64), prefix sums (3 ks u64), hopRC (u64 per alpha
 // hop), offA1, offB1 (u32), hopX (u16 per alpha hop), occupation lists (256 B)
 __host__ __device__ inline size_t warp_smem(const SysDev &d) {
-    return align16(size_t(d.sa + d.sb) * 12 + size_t(d.sa) * 10 + 192 * 8 + 256);
+    return align16(size_t(d.sa + d.sb) * 12 + size_t(d.sa) * 10 + size_t(3 * d.ks) * 8 + 256);
 }
 
 inline size_t emit_smem_bytes_w(const SysDev &d, int warps) {
@@ -131,7 +131,7 @@ __device__ __forceinline__ bool nonzero(double v) {
     return ((unsigned long long)__double_as_longlong(v) << 1) != 0ull;
 }
 
-constexpr int kU = 4;  // elements each lane carries per reservation round
+constexpr int kU = 2;  // elements each lane carries per reservation round
 
 __device__ __forceinline__ bool in_pass(const BucketOut &B, unsigned b) { return b >= B.lo && b < B.hi; }
 
@@ -306,7 +306,11 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
             if (!want[k]) continue;
             v[k] = __dmul_rn(e[k], c);
             tg[k] = ha[k] * cb + hb[k];
-            ok[k] = nonzero(v[k]) && !(fabs(v[k]) < o.b.eps_elem);
+            ok[k] = nonzero(v[k]);
+        }
+        if (o.b.eps_elem > 0.0) {  // heat-bath style screen (uniform branch: no FP64 compare when off)
+#pragma unroll
+            for (int k = 0; k < kU; ++k) ok[k] = ok[k] && !(fabs(v[k]) < o.b.eps_elem);
         }
         if (single >= 0) single_append(o.b, (unsigned)single, ok, tg, v);
         else warp_append(o.b, ok, bk, tg, v);
@@ -336,8 +340,8 @@ __device__ __forceinline__ void pair_prefix(const unsigned char *occ, int M, int
         const unsigned long long y2 = __shfl_up_sync(kFull, c2, w);
         if (lane >= w) c0 += y0, c1 += y1, c2 += y2;
     }
-    if (lane < M - 2) pre[lane + 1] = c0, pre[64 + lane + 1] = c1, pre[128 + lane + 1] = c2;
-    if (lane == 0) pre[0] = 0, pre[64] = 0, pre[128] = 0;
+    if (lane < M - 2) pre[lane + 1] = c0, pre[ks + lane + 1] = c1, pre[2 * ks + lane + 1] = c2;
+    if (lane == 0) pre[0] = 0, pre[ks] = 0, pre[2 * ks] = 0;
     __syncwarp();
 }
 
@@ -349,12 +353,12 @@ __device__ __forceinline__ unsigned long long pair_rank(unsigned long long rem, 
                                                         const unsigned long long *bt, int ks) {
     const int q1 = __popcll(rem & ((1ull << a) - 1ull));
     const int q2 = __popcll(rem & ((1ull << b) - 1ull));
-    return pre[q1] + bt[a * ks + q1 + 1] + pre[64 + q2] - pre[64 + q1] + bt[b * ks + q2 + 2] +
-           pre[128 + (M - 2)] - pre[128 + q2];
+    return pre[q1] + bt[a * ks + q1 + 1] + pre[ks + q2] - pre[ks + q1] + bt[b * ks + q2 + 2] +
+           pre[2 * ks + (M - 2)] - pre[2 * ks + q2];
 }
 
 template <int kMode>
-__global__ void __launch_bounds__(kEmitThreads, 3)
+__global__ void __launch_bounds__(kEmitThreads, 4)
 emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             const double *__restrict__ in_coef, long long n_in, const EmitOut o) {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -369,8 +373,8 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
     unsigned char *wb = sm + block_smem(d) + size_t(warp) * warp_smem(d);
     unsigned long long *rankA1 = reinterpret_cast<unsigned long long *>(wb);
     unsigned long long *rankB1 = rankA1 + d.sa;
-    unsigned long long *pre = rankB1 + d.sb;  // prefix sums A0 | A1 | A2, 64 each
-    unsigned long long *hopRC = pre + 192;    // bucket map entry of each kept alpha hop's row
+    unsigned long long *pre = rankB1 + d.sb;  // prefix sums A0 | A1 | A2, ks each
+    unsigned long long *hopRC = pre + 3 * ks;  // bucket map entry of each kept alpha hop's row
     unsigned *offA1 = reinterpret_cast<unsigned *>(hopRC + d.sa);
     unsigned *offB1 = offA1 + d.sa;
     unsigned short *hopX = reinterpret_cast<unsigned short *>(offB1 + d.sb);  // kept alpha hops
@@ -607,7 +611,7 @@ row_weight_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wb = sm + block_smem(d) + size_t(warp) * warp_smem(d);
     unsigned long long *pre = reinterpret_cast<unsigned long long *>(wb);
-    unsigned char *occA = reinterpret_cast<unsigned char *>(pre + 192);
+    unsigned char *occA = reinterpret_cast<unsigned char *>(pre + 3 * ks);
     unsigned char *virA = occA + 64, *occB = occA + 128, *virB = occA + 192;
     const unsigned char *pOA = pairs + 2 * d.pair_off[0], *pVA = pairs + 2 * d.pair_off[1];
     const unsigned long long cb = d.cb;

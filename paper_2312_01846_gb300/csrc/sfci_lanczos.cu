@@ -185,7 +185,7 @@ struct sfci_lanczos {
     double *msumsq = nullptr;
     unsigned *queue = nullptr;
     int *mstatus = nullptr;
-    double ms_emit = 0, ms_merge = 0, ms_plan = 0, budget_gb = 0;
+    double ms_emit = 0, ms_merge = 0, ms_plan = 0, budget_gb = 0, regions_gb = 0;
     double tau_prev = 0.0;             // previous truncation cut in u (0: none)
     std::vector<double> cut_at;        // truncation cut at each basis index of the last cycle
     unsigned long long stream_prev = 0;  // entries streamed by the previous merge
@@ -337,7 +337,10 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             if (!w) continue;
             if ((double)w > per_bucket) {
                 const unsigned long long ns = (unsigned long long)std::ceil((double)w / per_bucket);
-                const unsigned long long per = (unsigned long long)std::ceil(1.2 * (double)w / (double)ns) + 64;
+                // the beta hash splits w elements over ns buckets: mean w/ns, and
+                // four standard deviations of slack (the rest spills to the overflow list)
+                const double mu = (double)w / (double)ns;
+                const unsigned long long per = (unsigned long long)std::ceil(mu + 4.0 * std::sqrt(mu) + 32.0);
                 z->h_map[row] = ((unsigned long long)caps.size() << 32) | ns;
                 caps.insert(caps.end(), ns, per);
                 open = false;
@@ -458,6 +461,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         SFCI_CUDA(cudaStreamSynchronize(z->st));
         z->ms_plan = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan0).count();
         z->budget_gb = budget / 1e9;
+        z->regions_gb = (double)total_cap * sizeof(Slot) / 1e9;
         z->n_passes = npass;
         z->nb_log2 = 0;
         while ((1ull << z->nb_log2) < B) ++z->nb_log2;
@@ -721,6 +725,8 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
         info->ms_merge = z->ms_merge;
         info->ms_plan = z->ms_plan;
         info->n_passes = z->n_passes;
+        info->pass_budget_gb = z->budget_gb;
+        info->regions_gb = z->regions_gb;
         info->n_buckets_log2 = z->nb_log2;
         info->n_elements = n_in * (d.n_conn + 1);
         info->n_sigma = (long long)n_live;
