@@ -224,6 +224,9 @@ typedef struct sfci_step_info {
     int32_t reserved;
     double pass_budget_gb; /* device memory one pass's element regions may use (GB) */
     double regions_gb;     /* element regions of all buckets (GB): passes ~ this/budget */
+    double free_gb;        /* free device memory the plan saw, besides the solver's
+                              element, stream and overflow buffers (GB)              */
+    int64_t n_overflow;    /* most elements any pass sent past their bucket's region  */
 } sfci_step_info;
 
 typedef struct sfci_lanczos sfci_lanczos; /* opaque; owns w_0..w_{N_L-1}, T, S, table */

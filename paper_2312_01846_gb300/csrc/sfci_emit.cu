@@ -135,6 +135,22 @@ constexpr int kU = 2;  // elements each lane carries per reservation round
 
 __device__ __forceinline__ bool in_pass(const BucketOut &B, unsigned b) { return b >= B.lo && b < B.hi; }
 
+// Elements past their bucket's region go to the overflow list: the lanes that
+// overflow in one round reserve their places with one atomic (every lane calls it).
+__device__ __forceinline__ void overflow_append(const BucketOut &B, bool of, const ulonglong2 &sl) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(kFull, of);
+    if (!bal) return;
+    const int leader = __ffs(bal) - 1;
+    unsigned long long q0 = 0;
+    if ((int)lane == leader) q0 = atomicAdd(B.ovf_n, (unsigned long long)__popc(bal));
+    q0 = __shfl_sync(kFull, q0, leader);
+    if (!of) return;
+    const unsigned long long q = q0 + __popc(bal & ((1u << lane) - 1u));
+    if ((long long)q < B.ovf_cap) reinterpret_cast<ulonglong2 *>(B.ovf)[q] = sl;
+    else atomicOr(B.status, 2);
+}
+
 // Up to kU elements per lane (ok[k]) are appended to their buckets: the lanes
 // of the warp that share a bucket reserve their slots with one atomic, issued
 // for all k before any result is used, and write one run.
@@ -153,17 +169,15 @@ __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, 
     for (int k = 0; k < kU; ++k) base[k] = __shfl_sync(kFull, base[k], __ffs(peers[k]) - 1);
 #pragma unroll
     for (int k = 0; k < kU; ++k) {
-        if (!ok[k]) continue;
-        const unsigned pos = base[k] + __popc(peers[k] & lt);
-        const unsigned long long o0 = __ldg(&B.bk.boff[bk[k]]), o1 = __ldg(&B.bk.boff[bk[k] + 1]);
+        bool of = false;
         const ulonglong2 sl = make_ulonglong2(tg[k], (unsigned long long)__double_as_longlong(v[k]));
-        if (pos < o1 - o0) {
-            reinterpret_cast<ulonglong2 *>(B.elem)[o0 - B.base + pos] = sl;
-        } else {
-            const unsigned long long q = atomicAdd(B.ovf_n, 1ull);
-            if ((long long)q < B.ovf_cap) reinterpret_cast<ulonglong2 *>(B.ovf)[q] = sl;
-            else atomicOr(B.status, 2);
+        if (ok[k]) {
+            const unsigned pos = base[k] + __popc(peers[k] & lt);
+            const unsigned long long o0 = __ldg(&B.bk.boff[bk[k]]), o1 = __ldg(&B.bk.boff[bk[k] + 1]);
+            if (pos < o1 - o0) reinterpret_cast<ulonglong2 *>(B.elem)[o0 - B.base + pos] = sl;
+            else of = true;
         }
+        overflow_append(B, of, sl);
     }
 }
 
@@ -242,16 +256,14 @@ __device__ __forceinline__ void single_append(const BucketOut &B, unsigned b, co
     ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(B.elem) + (o0 - B.base);
 #pragma unroll
     for (int k = 0; k < kU; ++k) {
-        if (!ok[k]) continue;
-        const unsigned pos = base + pre[k];
+        bool of = false;
         const ulonglong2 sl = make_ulonglong2(tg[k], (unsigned long long)__double_as_longlong(v[k]));
-        if (pos < cap) {
-            dst[pos] = sl;
-        } else {
-            const unsigned long long q = atomicAdd(B.ovf_n, 1ull);
-            if ((long long)q < B.ovf_cap) reinterpret_cast<ulonglong2 *>(B.ovf)[q] = sl;
-            else atomicOr(B.status, 2);
+        if (ok[k]) {
+            const unsigned pos = base + pre[k];
+            if (pos < cap) dst[pos] = sl;
+            else of = true;
         }
+        overflow_append(B, of, sl);
     }
 }
 

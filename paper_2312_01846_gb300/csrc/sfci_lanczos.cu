@@ -167,6 +167,8 @@ struct sfci_lanczos {
     bool have_prev = false;
     double e_prev = 0.0;
     long long m_prev = 0, nin_prev = 0;
+    long long ovf_used = 0;  // most overflow elements of a pass in the last sigma
+    double elem_prev = 0.0;  // intermediate elements of the last sigma
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t evp[4] = {nullptr, nullptr, nullptr, nullptr};  // emit / merge timing
     // bucketed sigma (sfci_merge.cu); every buffer with its allocated bytes
@@ -185,7 +187,7 @@ struct sfci_lanczos {
     double *msumsq = nullptr;
     unsigned *queue = nullptr;
     int *mstatus = nullptr;
-    double ms_emit = 0, ms_merge = 0, ms_plan = 0, budget_gb = 0, regions_gb = 0;
+    double ms_emit = 0, ms_merge = 0, ms_plan = 0, budget_gb = 0, regions_gb = 0, free_gb = 0, held_gb = 0;
     double tau_prev = 0.0;             // previous truncation cut in u (0: none)
     std::vector<double> cut_at;        // truncation cut at each basis index of the last cycle
     unsigned long long stream_prev = 0;  // entries streamed by the previous merge
@@ -385,14 +387,22 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     // streamed-output capacity: 16 N_d (the merge raises the threshold to keep
     // the stream within it) plus room for u's entries on w_i, w_{i-1}
     double sig_need = std::min(16.0 * (double)z->nkeep, E) + 2.0 * (double)z->nkeep + 1024.0;
-    long long ovf_cap = std::max<long long>(1 << 20, z->ovf_cap);
+    // overflow list per pass: 1.5 times the most any pass of the previous sigma
+    // needed, grown by (element ratio)^0.75 when the input grew (a larger input
+    // also runs more passes), at least 2^20 entries; a list that proves short
+    // is grown and the sigma redone
+    long long ovf_cap = std::max<long long>(
+        1 << 20, (long long)(1.5 * (double)z->ovf_used *
+                             std::pow(std::max(1.0, E / std::max(1.0, z->elem_prev)), 0.75)));
     long long totp = 0;
     for (int j = 0; j <= i; ++j) totp += z->wn[j];
     for (int attempt = 0; attempt < 8; ++attempt) {
+        const double tau_start = tau;
         size_t free_b = 0, tot_b = 0;
         SFCI_CUDA(cudaMemGetInfo(&free_b, &tot_b));
         // memory the element regions may use: what is free plus what the big buffers hold
-        const double held = (double)z->belem.bytes + (double)z->sig_key.bytes + (double)z->sig_val.bytes;
+        const double held = (double)z->belem.bytes + (double)z->sig_key.bytes + (double)z->sig_val.bytes +
+                            (double)z->bovf.bytes + (double)z->bovf_sorted.bytes;
         double avail = 0.85 * ((double)free_b + held);
         if (z->p.mem_budget > 0) avail = std::min(avail, (double)z->p.mem_budget);
         const double budget = avail - 1.1 * sig_need * 16.0 - 2.0 * ovf_cap * 16.0;
@@ -413,11 +423,15 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         const int npass = (int)cuts.size() - 1;
         const size_t want_elem = size_t(max_pass) * sizeof(Slot);
         size_t want_sig = size_t(sig_need) * 8;
-        if (z->belem.bytes < want_elem || z->sig_key.bytes < want_sig || z->sig_val.bytes < want_sig) {
-            // the three large buffers are sized together from one budget: free them
-            // all, then give the sigma output 10 % headroom out of the same budget
+        const size_t want_ovf = size_t(ovf_cap) * sizeof(Slot);
+        if (z->belem.bytes < want_elem || z->sig_key.bytes < want_sig || z->sig_val.bytes < want_sig ||
+            z->bovf.bytes < want_ovf || z->bovf_sorted.bytes < want_ovf ||
+            z->bovf.bytes > 4 * want_ovf + (size_t(1) << 30)) {
+            // the large buffers (elements, stream, overflow lists) are sized together
+            // from one budget: free them all, then give the sigma output 10 % headroom
+            // out of the same budget
             SFCI_CUDA(cudaStreamSynchronize(z->st));
-            for (auto *bb : {&z->belem, &z->sig_key, &z->sig_val}) {
+            for (auto *bb : {&z->belem, &z->sig_key, &z->sig_val, &z->bovf, &z->bovf_sorted}) {
                 cudaFree(bb->p);
                 bb->p = nullptr;
                 bb->bytes = 0;
@@ -427,6 +441,9 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if ((r = ensure(z->sig_key, want_sig, z->st, "sigma keys"))) return r;
         if ((r = ensure(z->sig_val, want_sig, z->st, "sigma values"))) return r;
         z->sig_cap = (long long)(std::min(z->sig_key.bytes, z->sig_val.bytes) / 8);
+        if ((r = ensure(z->bovf, want_ovf, z->st, "overflow list"))) return r;
+        if ((r = ensure(z->bovf_sorted, want_ovf, z->st, "sorted overflow"))) return r;
+        z->ovf_cap = ovf_cap;
         if ((r = ensure(z->belem, want_elem, z->st, "element regions"))) return r;
         if ((r = ensure(z->bcount, size_t(B) * 4, z->st, "bucket counters", 1.5))) return r;
         if ((r = ensure(z->probes, size_t(std::max<long long>(totp, 1)) * sizeof(Probe), z->st, "probes"))) return r;
@@ -434,9 +451,6 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if ((r = ensure(z->poff, size_t(B + 1) * 8, z->st, "probe offsets", 1.5))) return r;
         if ((r = ensure(z->tmp_counts, size_t(B + 1) * 4, z->st, "overflow counts", 1.5))) return r;
         if ((r = ensure(z->ovf_off, size_t(B + 1) * 8, z->st, "overflow offsets", 1.5))) return r;
-        if ((r = ensure(z->bovf, size_t(ovf_cap) * sizeof(Slot), z->st, "overflow list"))) return r;
-        if ((r = ensure(z->bovf_sorted, size_t(ovf_cap) * sizeof(Slot), z->st, "sorted overflow"))) return r;
-        z->ovf_cap = ovf_cap;
         if ((r = ensure(z->scan_ws, scan_ws_bytes((long long)B + 1), z->st, "scan workspace", 1.5))) return r;
         for (int j = 0; j <= i; ++j)
             if (!z->sigw[j]) SFCI_CUDA(cudaMalloc(&z->sigw[j], size_t(z->nkeep) * 8));
@@ -461,11 +475,14 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         SFCI_CUDA(cudaStreamSynchronize(z->st));
         z->ms_plan = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_plan0).count();
         z->budget_gb = budget / 1e9;
+        z->free_gb = (double)free_b / 1e9;
+        z->held_gb = held / 1e9;
         z->regions_gb = (double)total_cap * sizeof(Slot) / 1e9;
         z->n_passes = npass;
         z->nb_log2 = 0;
         while ((1ull << z->nb_log2) < B) ++z->nb_log2;
         z->ms_emit = z->ms_merge = 0.0;
+        unsigned long long max_ovf = 0;  // most overflow elements of any pass
         for (int pass = 0; pass < npass; ++pass) {
             const unsigned lo = (unsigned)cuts[pass], hi = (unsigned)cuts[pass + 1];
             SFCI_CUDA(cudaMemsetAsync(z->ovf_n, 0, 8, z->st));
@@ -516,7 +533,11 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             A.status = z->mstatus;
             SFCI_CUDA(launch_merge(A, slots, z->st));
             SFCI_CUDA(cudaEventRecord(z->evp[2], z->st));
+            unsigned long long ovf_here = 0;
+            SFCI_CUDA(cudaMemcpyAsync(&ovf_here, z->ovf_n, 8, cudaMemcpyDeviceToHost, z->st));
             SFCI_CUDA(cudaEventSynchronize(z->evp[2]));
+            SFCI_CUDA(cudaStreamSynchronize(z->st));
+            max_ovf = std::max(max_ovf, ovf_here);
             float a = 0.f, b = 0.f;
             cudaEventElapsedTime(&a, z->evp[0], z->evp[1]);
             cudaEventElapsedTime(&b, z->evp[1], z->evp[2]);
@@ -538,17 +559,24 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if (hs == 0) {
             *n_out = ho, *n_live = hl, *n_nonzero = hz, *sumsq = hq;
             z->stream_prev = ho;
+            z->ovf_used = (long long)max_ovf;
+            z->elem_prev = E;
             return SFCI_OK;
         }
         if (hs & 16) {
             set_error("an intermediate element fell outside the row map");
             return SFCI_E_INVALID;
         }
+        if (hs & 2) {  // the overflow list was cut short: the merge saw part of it, redo
+            ovf_cap *= 4;  // (from the threshold this attempt started with)
+            tau = tau_start;
+            *tau_io = tau;
+            continue;
+        }
         if (hs & 4) {
             set_error("a merge bucket held more distinct entries than its table");
             return SFCI_E_CAPACITY;
         }
-        if (hs & 2) ovf_cap *= 4;
         // the stream outgrew its buffer before the raises caught up: redo from the
         // raised threshold (still at or below the N_d-th largest) with more room
         if (hs & 8) sig_need = std::max(sig_need * 2.0, (double)ho * 1.3 + 2.0 * z->nkeep);
@@ -727,6 +755,8 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
         info->n_passes = z->n_passes;
         info->pass_budget_gb = z->budget_gb;
         info->regions_gb = z->regions_gb;
+        info->free_gb = z->free_gb + z->held_gb;
+        info->n_overflow = z->ovf_used;
         info->n_buckets_log2 = z->nb_log2;
         info->n_elements = n_in * (d.n_conn + 1);
         info->n_sigma = (long long)n_live;

@@ -152,11 +152,26 @@ __global__ void ovf_scatter_kernel(Buckets bk, const Slot *ovf, const unsigned l
                                    unsigned *fill, Slot *out) {
     long long n = (long long)*ovf_n;
     if (n > ovf_cap) n = ovf_cap;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const ulonglong2 e = reinterpret_cast<const ulonglong2 *>(ovf)[i];
-        const unsigned b = bucket_key(bk, e.x) - lo;
-        const unsigned long long pos = off[b] + atomicAdd(&fill[b], 1u);
+    const unsigned lane = threadIdx.x & 31;
+    // whole warps iterate together so that the lanes sharing a bucket take
+    // their places with one atomic
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+        const long long i = i0 + lane;
+        const bool act = i < n;
+        ulonglong2 e = make_ulonglong2(0ull, 0ull);
+        unsigned b = 0;
+        if (act) {
+            e = reinterpret_cast<const ulonglong2 *>(ovf)[i];
+            b = bucket_key(bk, e.x) - lo;
+        }
+        const unsigned peers = __match_any_sync(kFull, act ? b : (0x80000000u | lane));
+        const int leader = __ffs(peers) - 1;
+        unsigned f0 = 0;
+        if (act && (int)lane == leader) f0 = atomicAdd(&fill[b], (unsigned)__popc(peers));
+        f0 = __shfl_sync(kFull, f0, leader);
+        if (!act) continue;
+        const unsigned long long pos = off[b] + f0 + __popc(peers & ((1u << lane) - 1u));
         // offsets count every overflowing element; a truncated list (status
         // bit 1, the sigma is redone) must not write past its end
         if ((long long)pos < ovf_cap) reinterpret_cast<ulonglong2 *>(out)[pos] = e;
