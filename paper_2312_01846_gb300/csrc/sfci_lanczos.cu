@@ -405,7 +405,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                             (double)z->bovf.bytes + (double)z->bovf_sorted.bytes;
         double avail = 0.85 * ((double)free_b + held);
         if (z->p.mem_budget > 0) avail = std::min(avail, (double)z->p.mem_budget);
-        const double budget = avail - 1.1 * sig_need * 16.0 - 2.0 * ovf_cap * 16.0;
+        const double budget = avail - 1.1 * sig_need * 16.0 - 3.0 * ovf_cap * 16.0;  // two overflow lists with 50 % headroom
         // passes: contiguous bucket ranges whose regions fit the budget
         std::vector<unsigned long long> cuts{0};
         unsigned long long max_pass = 0;
@@ -426,7 +426,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         const size_t want_ovf = size_t(ovf_cap) * sizeof(Slot);
         if (z->belem.bytes < want_elem || z->sig_key.bytes < want_sig || z->sig_val.bytes < want_sig ||
             z->bovf.bytes < want_ovf || z->bovf_sorted.bytes < want_ovf ||
-            z->bovf.bytes > 4 * want_ovf + (size_t(1) << 30)) {
+            z->bovf.bytes > 8 * want_ovf + (size_t(4) << 30)) {
             // the large buffers (elements, stream, overflow lists) are sized together
             // from one budget: free them all, then give the sigma output 10 % headroom
             // out of the same budget
@@ -441,8 +441,11 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if ((r = ensure(z->sig_key, want_sig, z->st, "sigma keys"))) return r;
         if ((r = ensure(z->sig_val, want_sig, z->st, "sigma values"))) return r;
         z->sig_cap = (long long)(std::min(z->sig_key.bytes, z->sig_val.bytes) / 8);
-        if ((r = ensure(z->bovf, want_ovf, z->st, "overflow list"))) return r;
-        if ((r = ensure(z->bovf_sorted, want_ovf, z->st, "sorted overflow"))) return r;
+        // the overflow lists get 50 % headroom, so small changes in overflow
+        // do not reallocate the whole group
+        if ((r = ensure(z->bovf, want_ovf, z->st, "overflow list", 1.5))) return r;
+        if ((r = ensure(z->bovf_sorted, want_ovf, z->st, "sorted overflow", 1.5))) return r;
+        ovf_cap = (long long)(std::min(z->bovf.bytes, z->bovf_sorted.bytes) / sizeof(Slot));
         z->ovf_cap = ovf_cap;
         if ((r = ensure(z->belem, want_elem, z->st, "element regions"))) return r;
         if ((r = ensure(z->bcount, size_t(B) * 4, z->st, "bucket counters", 1.5))) return r;
