@@ -252,6 +252,14 @@ sfci_status sfci_system_create(sfci_system **out, int n, int na, int nb, const d
     d.pairs = reinterpret_cast<const unsigned char *>(blk + off_p);
     d.hf = fp32 ? reinterpret_cast<const float *>(blk + off_hf) : nullptr;
     d.gf = fp32 ? reinterpret_cast<const float *>(blk + off_gf) : nullptr;
+    {
+        // |<D'|H|D>| <= |e_core| + N max|h| + N^2 max|g| (diagonal, singles and doubles)
+        double mh = 0.0, mg = 0.0;
+        for (size_t i = 0; i < nh; ++i) mh = std::max(mh, std::fabs(h_host[i]));
+        for (size_t i = 0; i < ng; ++i) mg = std::max(mg, std::fabs(g_host[i]));
+        const double N = (double)(na + nb);
+        d.hbound = (std::fabs(e_core) + N * mh + N * N * mg) * (1.0 + 1e-6);
+    }
     d.bound_ab = reinterpret_cast<const double *>(blk + off_bab);
     d.bound_ss = reinterpret_cast<const double *>(blk + off_bss);
     s->d = d;

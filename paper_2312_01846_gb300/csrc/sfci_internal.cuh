@@ -58,6 +58,7 @@ struct SysDev {
     // for every (b, j); bound_ss[i*n+j] >= |(ai|bj) - (aj|bi)| for every (a, b)
     const double *bound_ab;
     const double *bound_ss;
+    double hbound;       // |<D'|H|D>| <= hbound for every pair of determinants
 };
 
 }  // namespace sfci
@@ -373,11 +374,13 @@ struct MergeArgs {
     unsigned long long *mark;
     int *lock;
     long long nkeep;
+    int fix_shift;                      // S: sigma entries are summed exactly in units of 2^-S
     double *sumsq;                      // sum of u^2 over the non-zero entries off w_i, w_{i-1}
     unsigned long long *n_live;         // entries that survive the screen
     unsigned long long *n_nonzero;      // non-zero entries off w_i, w_{i-1} (streamed or not)
     unsigned *queue;
-    int *status;                        // bit 2: a bucket has too many distinct keys; bit 3: output full
+    int *status;                        // bit 2: a bucket has too many distinct keys; bit 3: output full;
+                                        // bit 5: an element outside the 2^-S fixed-point range
 };
 // magnitude bins of |u|: the top 14 bits of the IEEE bit pattern (11 exponent
 // bits, 2 mantissa bits: quarter octaves) of a non-negative double

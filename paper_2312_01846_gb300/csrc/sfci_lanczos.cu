@@ -396,6 +396,10 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                              std::pow(std::max(1.0, E / std::max(1.0, z->elem_prev)), 0.75)));
     long long totp = 0;
     for (int j = 0; j <= i; ++j) totp += z->wn[j];
+    // fixed-point unit of the exact sums: sigma entries are bounded by
+    // (n_conn + 1) hbound max|c|, and the basis vectors are normalised (|c| <= 1)
+    int fix_shift = (int)std::floor(125.0 - std::log2(std::max(1e-300, (double)(d.n_conn + 1) * d.hbound)));
+    fix_shift = std::max(-900, std::min(1000, fix_shift));
     for (int attempt = 0; attempt < 8; ++attempt) {
         const double tau_start = tau;
         size_t free_b = 0, tot_b = 0;
@@ -529,6 +533,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             A.mark = z->mark_w;
             A.lock = z->lock_w;
             A.nkeep = z->nkeep;
+            A.fix_shift = fix_shift;
             A.sumsq = z->msumsq;
             A.n_live = z->mlive;
             A.n_nonzero = z->nnz;
@@ -569,6 +574,12 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if (hs & 16) {
             set_error("an intermediate element fell outside the row map");
             return SFCI_E_INVALID;
+        }
+        if (hs & 32) {  // an element beyond the fixed-point range (an input not normalised): coarser units
+            fix_shift -= 16;
+            tau = tau_start;
+            *tau_io = tau;
+            continue;
         }
         if (hs & 2) {  // the overflow list was cut short: the merge saw part of it, redo
             ovf_cap *= 4;  // (from the threshold this attempt started with)

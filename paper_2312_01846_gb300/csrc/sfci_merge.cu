@@ -54,6 +54,79 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
 
+// ------------------------------------------------------------- exact sums
+// Each sigma entry is accumulated as a 128-bit two's-complement integer in
+// units of 2^-S (S chosen by the host so that no sum leaves the range): an
+// element v = m 2^e (m < 2^53) becomes m 2^(e+S), exactly unless e + S < 0
+// (|v| below 2^(52-S), rounded to the nearest unit).  Integer atomics add
+// them, so the sum is exact and independent of the order of the adds, and one
+// correctly rounded conversion gives the entry's double.
+
+struct Fix128 {
+    unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ Fix128 to_fixed(double v, int S, bool &range_ok) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
+    int ex = (int)((bits >> 52) & 0x7FF);
+    Fix128 x{0ull, 0ull};
+    if (ex == 0 && mant == 0) return x;
+    if (ex) mant |= 1ull << 52;
+    else ex = 1;
+    const int sh = ex - 1075 + S;  // v = mant 2^(ex-1075)
+    if (sh > 74) {                 // would not fit in 127 bits
+        range_ok = false;
+        return x;
+    }
+    if (sh >= 64) {
+        x.hi = mant << (sh - 64);
+    } else if (sh > 0) {
+        x.lo = mant << sh;
+        x.hi = mant >> (64 - sh);
+    } else if (sh == 0) {
+        x.lo = mant;
+    } else if (-sh <= 63) {
+        const int r = -sh;
+        x.lo = (mant >> r) + ((mant >> (r - 1)) & 1ull);  // nearest, ties away from zero
+    }
+    if (bits >> 63) {  // negate
+        x.lo = ~x.lo + 1ull;
+        x.hi = ~x.hi + (x.lo == 0ull ? 1ull : 0ull);
+    }
+    return x;
+}
+
+// the sum held in (lo, hi) as a double, rounded to nearest, ties to even
+__device__ __forceinline__ double from_fixed(unsigned long long lo, unsigned long long hi, int S) {
+    const bool neg = (long long)hi < 0;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    if (hi == 0ull && lo == 0ull) return 0.0;
+    int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading bit
+    unsigned long long m;
+    if (p <= 52) {
+        m = lo << (52 - p);
+    } else {
+        const int sh = p - 52;  // 1..74
+        m = sh >= 64 ? hi >> (sh - 64) : (lo >> sh) | (hi << (64 - sh));
+        const int g = sh - 1;   // guard bit position
+        const unsigned long long gbit = g >= 64 ? (hi >> (g - 64)) & 1ull : (lo >> g) & 1ull;
+        const bool sticky = g >= 64 ? (lo != 0ull || (hi & ((1ull << (g - 64)) - 1ull)) != 0ull)
+                                    : (lo & ((1ull << g) - 1ull)) != 0ull;
+        if (gbit && (sticky || (m & 1ull))) ++m;
+        if (m >> 53) {
+            m >>= 1;
+            ++p;
+        }
+    }
+    const unsigned long long bexp = (unsigned long long)(p - S + 1023);
+    const unsigned long long bits = ((unsigned long long)neg << 63) | (bexp << 52) | (m & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
+}
+
 // ------------------------------------------------------------- scan
 
 // exclusive scan of unsigned 32-bit counts into 64-bit offsets, m entries,
@@ -276,8 +349,9 @@ __global__ void __launch_bounds__(kMT)
 merge_kernel(MergeArgs A) {
     extern __shared__ __align__(16) unsigned char msm[];
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(msm);
-    double *vals = reinterpret_cast<double *>(keys + kSlots);
-    unsigned short *occ = reinterpret_cast<unsigned short *>(vals + kSlots);
+    unsigned long long *acc_lo = keys + kSlots;  // exact sums, low and high words
+    unsigned long long *acc_hi = acc_lo + kSlots;
+    unsigned short *occ = reinterpret_cast<unsigned short *>(acc_hi + kSlots);
     unsigned char *flag = reinterpret_cast<unsigned char *>(occ + kSlots);
     __shared__ unsigned cur, n_occ;
     __shared__ unsigned long long s_tau;
@@ -286,7 +360,9 @@ merge_kernel(MergeArgs A) {
     const bool screen = A.eps > 0.0;
     // thresholds compared on bit patterns (|x| < t for t >= 0, NaN never below)
     const unsigned long long eps_bits = abs_bits(A.eps);
-    for (int sl = tid; sl < kSlots; sl += kMT) keys[sl] = kEmpty, vals[sl] = 0.0, flag[sl] = 0;
+    for (int sl = tid; sl < kSlots; sl += kMT) keys[sl] = kEmpty, acc_lo[sl] = 0ull, acc_hi[sl] = 0ull, flag[sl] = 0;
+    const int S = A.fix_shift;
+    bool range_ok = true;
     if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u), s_tau = *(volatile unsigned long long *)A.tau_bits;
     double sq = 0.0;
     unsigned long long n_live = 0, n_nonzero = 0;
@@ -351,8 +427,13 @@ merge_kernel(MergeArgs A) {
                     if (ins) occ[base + __popc(bal & lt)] = (unsigned short)h;
                 }
                 if (act) {
-                    if (found) atomicAdd(&vals[h], __longlong_as_double((long long)x[k].y));
-                    else atomicOr(A.status, 4);
+                    if (found) {
+                        const Fix128 f = to_fixed(__longlong_as_double((long long)x[k].y), S, range_ok);
+                        const unsigned long long old = atomicAdd(&acc_lo[h], f.lo);
+                        atomicAdd(&acc_hi[h], f.hi + (old + f.lo < old ? 1ull : 0ull));  // with the carry
+                    } else {
+                        atomicOr(A.status, 4);
+                    }
                 }
             }
         }
@@ -372,7 +453,7 @@ merge_kernel(MergeArgs A) {
                 if (c == kEmpty) break;
                 h = (h + 1) & (kSlots - 1);
             }
-            double sv = found >= 0 ? vals[found] : 0.0;
+            double sv = found >= 0 ? from_fixed(acc_lo[found], acc_hi[found], S) : 0.0;
             if (screen && abs_bits(sv) < eps_bits) sv = 0.0;  // screened entries count as absent
             const int j = (int)(pr.where >> 40);
             const long long k = (long long)(pr.where & ((1ull << 40) - 1));
@@ -392,7 +473,7 @@ merge_kernel(MergeArgs A) {
             if (t < nocc) {
                 const unsigned sl = occ[t];
                 key = keys[sl];
-                v = vals[sl];
+                v = from_fixed(acc_lo[sl], acc_hi[sl], S);
                 const unsigned long long ab = abs_bits(v);
                 live = !(screen && ab < eps_bits);
                 const bool nz = live && !flag[sl] && ab != 0ull;
@@ -401,7 +482,7 @@ merge_kernel(MergeArgs A) {
                     sq = __fma_rn(v, v, sq);
                 }
                 w = nz && !(ab < tau_bits);
-                keys[sl] = kEmpty, vals[sl] = 0.0, flag[sl] = 0;
+                keys[sl] = kEmpty, acc_lo[sl] = 0ull, acc_hi[sl] = 0ull, flag[sl] = 0;
                 if (w) hb = (unsigned)(ab >> kHistShift);
             }
             // histogram of the streamed entries (lanes sharing a bin add once)
@@ -448,9 +529,10 @@ merge_kernel(MergeArgs A) {
         atomicAdd(A.n_live, n_live);
         atomicAdd(A.n_nonzero, n_nonzero);
     }
+    if (!range_ok) atomicOr(A.status, 32);
 }
 
-constexpr size_t merge_smem(int slots) { return size_t(slots) * (8 + 8 + 2 + 1); }
+constexpr size_t merge_smem(int slots) { return size_t(slots) * (8 + 16 + 2 + 1); }
 
 // ------------------------------------------------------------- u entries
 
