@@ -404,7 +404,7 @@ def run_ours(a):
     def brief(i):
         return {k: i[k] for k in ("n_in", "n_sigma", "n_passes", "ms_plan", "ms_emit", "ms_merge",
                                   "ms_topk", "ms_step", "redo", "tau", "cut", "pass_budget_gb",
-                                  "regions_gb", "free_gb", "n_overflow")}
+                                  "regions_gb", "free_gb", "n_overflow", "ms_alloc")}
 
     warm = []
     for _ in range(a.warmup):

@@ -227,6 +227,7 @@ typedef struct sfci_step_info {
     double free_gb;        /* free device memory the plan saw, besides the solver's
                               element, stream and overflow buffers (GB)              */
     int64_t n_overflow;    /* most elements any pass sent past their bucket's region  */
+    double ms_alloc;       /* of ms_plan: device buffer (re)allocation               */
 } sfci_step_info;
 
 typedef struct sfci_lanczos sfci_lanczos; /* opaque; owns w_0..w_{N_L-1}, T, S, table */

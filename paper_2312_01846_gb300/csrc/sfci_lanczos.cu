@@ -187,7 +187,8 @@ struct sfci_lanczos {
     double *msumsq = nullptr;
     unsigned *queue = nullptr;
     int *mstatus = nullptr;
-    double ms_emit = 0, ms_merge = 0, ms_plan = 0, budget_gb = 0, regions_gb = 0, free_gb = 0, held_gb = 0;
+    double ms_emit = 0, ms_merge = 0, ms_plan = 0, budget_gb = 0, regions_gb = 0, free_gb = 0, held_gb = 0,
+           ms_alloc = 0;
     double tau_prev = 0.0;             // previous truncation cut in u (0: none)
     std::vector<double> cut_at;        // truncation cut at each basis index of the last cycle
     unsigned long long stream_prev = 0;  // entries streamed by the previous merge
@@ -305,6 +306,7 @@ constexpr unsigned long long kMaxRows = 1ull << 26;
 sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long long *n_out,
                            unsigned long long *n_live, unsigned long long *n_nonzero, double *sumsq) {
     double tau = *tau_io;
+    z->ms_alloc = 0.0;
     const SysDev &d = z->sys->d;
     const long long n_in = z->wn[i];
     const double E = (double)n_in * (double)(d.n_conn + 1);
@@ -427,6 +429,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         const int npass = (int)cuts.size() - 1;
         const size_t want_elem = size_t(max_pass) * sizeof(Slot);
         size_t want_sig = size_t(sig_need) * 8;
+        const auto t_alloc0 = std::chrono::steady_clock::now();
         const size_t want_ovf = size_t(ovf_cap) * sizeof(Slot);
         if (z->belem.bytes < want_elem || z->sig_key.bytes < want_sig || z->sig_val.bytes < want_sig ||
             z->bovf.bytes < want_ovf || z->bovf_sorted.bytes < want_ovf ||
@@ -461,6 +464,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if ((r = ensure(z->scan_ws, scan_ws_bytes((long long)B + 1), z->st, "scan workspace", 1.5))) return r;
         for (int j = 0; j <= i; ++j)
             if (!z->sigw[j]) SFCI_CUDA(cudaMalloc(&z->sigw[j], size_t(z->nkeep) * 8));
+        z->ms_alloc += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_alloc0).count();
         (void)total_cap;
         (void)hash_cap;
 
@@ -771,6 +775,7 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
         info->regions_gb = z->regions_gb;
         info->free_gb = z->free_gb + z->held_gb;
         info->n_overflow = z->ovf_used;
+        info->ms_alloc = z->ms_alloc;
         info->n_buckets_log2 = z->nb_log2;
         info->n_elements = n_in * (d.n_conn + 1);
         info->n_sigma = (long long)n_live;

@@ -301,9 +301,9 @@ __global__ void uniform_offsets_kernel(unsigned long long *boff, unsigned long l
 // while other CTAs still add, so they only undercount: the threshold is never
 // too high), then tau = max(tau, lower edge of b) and the next mark halfway
 // between out_n and out_cap; releases the lock.
-__device__ __noinline__ void raise_threshold(const MergeArgs &A, int tid, int *s_bin) {
+__device__ __noinline__ void raise_threshold(const MergeArgs &A, int tid, int *s_bin,
+                                             unsigned long long *part) {
     constexpr int per = kHistBins / kMT;  // bins per thread, thread 0 owns the top ones
-    __shared__ unsigned long long part[kMT];
     unsigned long long sum = 0;
     const int top = kHistBins - 1 - tid * per;
     for (int q = 0; q < per; ++q) sum += *(volatile unsigned long long *)&A.hist[top - q];
@@ -515,7 +515,8 @@ merge_kernel(MergeArgs A) {
             if (on >= *(volatile unsigned long long *)A.mark && atomicCAS(A.lock, 0, 1) == 0) s_raise = 1;
         }
         __syncthreads();
-        if (s_raise) raise_threshold(A, tid, &s_bin);
+        // (the bucket's occupied-slot list is spent: its shared memory holds the partial sums)
+        if (s_raise) raise_threshold(A, tid, &s_bin, reinterpret_cast<unsigned long long *>(occ));
         if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u), s_tau = *(volatile unsigned long long *)A.tau_bits;
         __syncthreads();
     }
