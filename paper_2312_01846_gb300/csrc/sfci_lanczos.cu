@@ -191,6 +191,7 @@ struct sfci_lanczos {
            ms_alloc = 0;
     double tau_prev = 0.0;             // previous truncation cut in u (0: none)
     std::vector<double> cut_at;        // truncation cut at each basis index of the last cycle
+    std::vector<long long> ovf_at;     // most overflow of a pass at each basis index of the last cycle
     unsigned long long stream_prev = 0;  // entries streamed by the previous merge
     unsigned long long *nnz = nullptr;  // device word: non-zero entries off w_i, w_{i-1}
     unsigned long long *tau_w = nullptr, *mark_w = nullptr;  // stream threshold bits, raise mark
@@ -393,9 +394,12 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     // needed, grown by (element ratio)^0.75 when the input grew (a larger input
     // also runs more passes), at least 2^20 entries; a list that proves short
     // is grown and the sigma redone
+    // (and at least what this basis index needed one cycle earlier: a cycle's
+    // first vector, the restart, concentrates sigma and overflows most)
+    const double at_i = i < (int)z->ovf_at.size() ? (double)z->ovf_at[i] : 0.0;
     long long ovf_cap = std::max<long long>(
-        1 << 20, (long long)(1.5 * (double)z->ovf_used *
-                             std::pow(std::max(1.0, E / std::max(1.0, z->elem_prev)), 0.75)));
+        1 << 20, (long long)(1.5 * std::max(at_i, (double)z->ovf_used *
+                                                std::pow(std::max(1.0, E / std::max(1.0, z->elem_prev)), 0.75))));
     long long totp = 0;
     for (int j = 0; j <= i; ++j) totp += z->wn[j];
     // fixed-point unit of the exact sums: sigma entries are bounded by
@@ -572,6 +576,8 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             *n_out = ho, *n_live = hl, *n_nonzero = hz, *sumsq = hq;
             z->stream_prev = ho;
             z->ovf_used = (long long)max_ovf;
+            if ((int)z->ovf_at.size() <= i) z->ovf_at.resize(i + 1, 0);
+            z->ovf_at[i] = (long long)max_ovf;
             z->elem_prev = E;
             return SFCI_OK;
         }
