@@ -215,7 +215,8 @@ typedef struct sfci_step_info {
     double ms_merge;   /* of ms_sigma: overflow sort + merge kernel (all passes)    */
     double ms_plan;    /* host time planning the merge buckets and buffers          */
     double ms_topk;    /* device time of the truncation (u entries, top-k, sort)    */
-    int32_t n_passes;  /* passes over the sources that sigma needed (memory bound)  */
+    int32_t n_passes;  /* passes over the sources that sigma needed (memory bound, plus
+                          passes split because their overflow outgrew the list) */
     int32_t n_buckets_log2; /* ceil(log2(merge buckets))                            */
     double tau;        /* stream threshold of the accepted attempt (entries of sigma
                           below it were not written out; see sfci_lanczos_step)  */

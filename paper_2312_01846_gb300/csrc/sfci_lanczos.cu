@@ -192,6 +192,7 @@ struct sfci_lanczos {
     double tau_prev = 0.0;             // previous truncation cut in u (0: none)
     std::vector<double> cut_at;        // truncation cut at each basis index of the last cycle
     std::vector<long long> ovf_at;     // most overflow of a pass at each basis index of the last cycle
+    int n_split = 0;                   // pass ranges split because their overflow outgrew the list
     unsigned long long stream_prev = 0;  // entries streamed by the previous merge
     unsigned long long *nnz = nullptr;  // device word: non-zero entries off w_i, w_{i-1}
     unsigned long long *tau_w = nullptr, *mark_w = nullptr;  // stream threshold bits, raise mark
@@ -498,8 +499,14 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         while ((1ull << z->nb_log2) < B) ++z->nb_log2;
         z->ms_emit = z->ms_merge = 0.0;
         unsigned long long max_ovf = 0;  // most overflow elements of any pass
-        for (int pass = 0; pass < npass; ++pass) {
-            const unsigned lo = (unsigned)cuts[pass], hi = (unsigned)cuts[pass + 1];
+        z->n_split = 0;
+        // passes as bucket ranges; a range whose overflow outgrew the list is
+        // split in two and emitted again (its merge has not run yet)
+        std::vector<std::pair<unsigned, unsigned>> ranges;
+        for (int pass = npass - 1; pass >= 0; --pass) ranges.emplace_back((unsigned)cuts[pass], (unsigned)cuts[pass + 1]);
+        while (!ranges.empty()) {
+            const unsigned lo = ranges.back().first, hi = ranges.back().second;
+            ranges.pop_back();
             SFCI_CUDA(cudaMemsetAsync(z->ovf_n, 0, 8, z->st));
             BucketOut bo;
             bo.bk = bk;
@@ -515,6 +522,29 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             SFCI_CUDA(cudaEventRecord(z->evp[0], z->st));
             SFCI_CUDA(launch_emit_buckets(d, z->wr[i], z->wc[i], n_in, bo, z->st, z->p.emit_warps));
             SFCI_CUDA(cudaEventRecord(z->evp[1], z->st));
+            if (hi - lo > 1) {
+                unsigned long long on = 0;
+                SFCI_CUDA(cudaMemcpyAsync(&on, z->ovf_n, 8, cudaMemcpyDeviceToHost, z->st));
+                SFCI_CUDA(cudaStreamSynchronize(z->st));
+                if ((long long)on > z->ovf_cap) {
+                    int hs2 = 0;
+                    SFCI_CUDA(cudaMemcpyAsync(&hs2, z->mstatus, 4, cudaMemcpyDeviceToHost, z->st));
+                    SFCI_CUDA(cudaStreamSynchronize(z->st));
+                    hs2 &= ~2;  // the list's truncation bit: this range is redone in halves
+                    SFCI_CUDA(cudaMemcpyAsync(z->mstatus, &hs2, 4, cudaMemcpyHostToDevice, z->st));
+                    SFCI_CUDA(cudaMemsetAsync(P<unsigned>(z->bcount) + lo, 0, size_t(hi - lo) * 4, z->st));
+                    unsigned mid = lo + 1;
+                    const unsigned long long half = (z->h_boff[lo] + z->h_boff[hi]) / 2;
+                    while (mid + 1 < hi && z->h_boff[mid] < half) ++mid;
+                    ranges.emplace_back(mid, hi);
+                    ranges.emplace_back(lo, mid);
+                    float a = 0.f;
+                    cudaEventElapsedTime(&a, z->evp[0], z->evp[1]);
+                    z->ms_emit += a;
+                    ++z->n_split;
+                    continue;
+                }
+            }
             SFCI_CUDA(sort_overflow(bk, P<unsigned>(z->bcount), lo, hi - lo, P<Slot>(z->bovf), z->ovf_n,
                                     z->ovf_cap, P<unsigned>(z->tmp_counts), P<unsigned long long>(z->ovf_off),
                                     z->scan_ws.p, P<Slot>(z->bovf_sorted), z->st));
@@ -559,6 +589,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             cudaEventElapsedTime(&b, z->evp[1], z->evp[2]);
             z->ms_emit += a, z->ms_merge += b;
         }
+        z->n_passes = npass + z->n_split;  // each split adds a pass
         int hs = 0;
         unsigned long long ho = 0, hl = 0, hz = 0;
         double hq = 0.0;
