@@ -220,6 +220,7 @@ template <int kMode>
 __device__ __forceinline__ bool wanted(const EmitOut &o, unsigned long long ha, unsigned long long hb,
                                        unsigned &b) {
     if (kMode != kModeBucket) return true;
+    if (ha < o.b.row_lo || ha > o.b.row_hi) return false;
     b = bucket_ab(o.b.bk, ha, hb);
     if (b == kNoBucket) {
         atomicOr(o.b.status, 16);
@@ -439,7 +440,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             bool keep = false;
             unsigned long long rcv = 0;
             if (x < d.sa) {
-                if (kMode == kModeBucket) {
+                if (kMode == kModeBucket && rankA1[x] >= o.b.row_lo && rankA1[x] <= o.b.row_hi) {
                     const RowCtx rc = row_ctx(o.b, rankA1[x]);
                     keep = ctx_in_pass(o.b, rc);
                     rcv = (unsigned long long)rc.first << 32 | rc.ns;
@@ -449,7 +450,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                         keep = !(fabs(c) * __ldg(&d.bound_ab[virA[iv] * n + occA[io]]) < o.b.eps_elem);
                     }
                 } else {
-                    keep = true;
+                    keep = kMode != kModeBucket;
                 }
             }
             const unsigned bal = __ballot_sync(kFull, keep);
@@ -462,8 +463,9 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
         }
         __syncwarp();
         // the source's own row: first bucket and count read once
-        const RowCtx rs = kMode == kModeBucket ? row_ctx(o.b, hA) : RowCtx{0u, 0u};
-        const bool self_row = kMode != kModeBucket || ctx_in_pass(o.b, rs);
+        const bool self_in = kMode != kModeBucket || (hA >= o.b.row_lo && hA <= o.b.row_hi);
+        const RowCtx rs = kMode == kModeBucket && self_in ? row_ctx(o.b, hA) : RowCtx{0u, 0u};
+        const bool self_row = kMode != kModeBucket || (self_in && ctx_in_pass(o.b, rs));
         const long long self_single = kMode == kModeBucket && rs.ns == 1 ? (long long)rs.first : -1;
 
         bool want[kU];

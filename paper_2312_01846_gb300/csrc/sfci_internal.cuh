@@ -249,6 +249,9 @@ struct BucketOut {
     unsigned long long *ovf_n;
     long long ovf_cap;
     unsigned lo, hi;
+    // alpha rows that can hold buckets [lo, hi) (row mode; rows without buckets
+    // between two passes belong to both): a target outside needs no row-map load
+    unsigned long long row_lo, row_hi;
     int *status;              // bit 1: overflow list full; bit 4: an element had no bucket
 };
 

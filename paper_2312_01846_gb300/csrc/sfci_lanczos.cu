@@ -179,6 +179,7 @@ struct sfci_lanczos {
     Buf bcount, belem, bovf, bovf_sorted, tmp_counts, ovf_off, probes, pcount, poff, scan_ws,
         sig_key, sig_val, cand_key, cand_val, weights, rowmap, boff;
     std::vector<unsigned long long> h_weights, h_map, h_boff;
+    std::vector<unsigned long long> h_nzrow, h_nzmap;  // rows with buckets and their map entries
     long long sig_cap = 0, ovf_cap = 0, cand_cap = 0;
     double *sigw[kMaxVec] = {};
     char *words = nullptr;  // hist[kHistBins] | outn | mlive | ovf_n | cand_n | msumsq | queue | mstatus | nnz | dmin | tau | mark | lock
@@ -361,6 +362,11 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             acc += (double)w;
             z->h_map[row] = ((unsigned long long)(caps.size() - 1) << 32) | 1ull;
         }
+        // rows with buckets, in row (and bucket) order, for the pass row ranges
+        z->h_nzrow.clear();
+        z->h_nzmap.clear();
+        for (unsigned long long row = 0; row < nrows; ++row)
+            if (z->h_map[row]) z->h_nzrow.push_back(row), z->h_nzmap.push_back(z->h_map[row]);
         B = caps.size();
         if (B >= (1ull << 31)) {
             set_error("too many merge buckets");
@@ -518,6 +524,25 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             bo.ovf_n = z->ovf_n;
             bo.ovf_cap = z->ovf_cap;
             bo.lo = lo, bo.hi = hi;
+            bo.row_lo = 0, bo.row_hi = ~0ull;
+            if (row_mode) {
+                // rows are bucketed in order: the rows before the first one with a
+                // bucket at or above lo, and from the first one with a bucket at or
+                // above hi on, hold no bucket of this pass
+                auto last_b = [&](size_t k) { return (z->h_nzmap[k] >> 32) + (unsigned)z->h_nzmap[k]; };
+                size_t a = 0, e = z->h_nzrow.size();
+                while (a < e) {
+                    const size_t m = (a + e) / 2;
+                    if (last_b(m) > lo) e = m; else a = m + 1;
+                }
+                bo.row_lo = a == 0 ? 0ull : z->h_nzrow[a - 1] + 1;
+                a = 0, e = z->h_nzrow.size();
+                while (a < e) {
+                    const size_t m = (a + e) / 2;
+                    if ((z->h_nzmap[m] >> 32) >= hi) e = m; else a = m + 1;
+                }
+                bo.row_hi = a == z->h_nzrow.size() ? d.ca - 1 : z->h_nzrow[a] - 1;
+            }
             bo.status = z->mstatus;
             SFCI_CUDA(cudaEventRecord(z->evp[0], z->st));
             SFCI_CUDA(launch_emit_buckets(d, z->wr[i], z->wc[i], n_in, bo, z->st, z->p.emit_warps));
