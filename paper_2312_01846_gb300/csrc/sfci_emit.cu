@@ -35,10 +35,11 @@ __host__ __device__ inline size_t block_smem(const SysDev &d) {
     return align16(size_t(d.n + 1) * d.ks * 8) + align16(size_t(d.n_pairs) * 2);
 }
 
-// per warp: rankA1, rankB1 (u64), prefix sums (3 ks u64), hopRC (u64 per alpha
-// hop), offA1, offB1 (u32), hopX (u16 per alpha hop), occupation lists (256 B)
+// per warp: overflow chunk cursor (2 u64), rankA1, rankB1 (u64), prefix sums
+// (3 ks u64), hopRC (u64 per alpha hop), offA1, offB1 (u32), hopX (u16 per
+// alpha hop), occupation lists (256 B)
 __host__ __device__ inline size_t warp_smem(const SysDev &d) {
-    return align16(size_t(d.sa + d.sb) * 12 + size_t(d.sa) * 10 + size_t(3 * d.ks) * 8 + 256);
+    return align16(16 + size_t(d.sa + d.sb) * 12 + size_t(d.sa) * 10 + size_t(3 * d.ks) * 8 + 256);
 }
 
 inline size_t emit_smem_bytes_w(const SysDev &d, int warps) {
@@ -135,18 +136,38 @@ constexpr int kU = 2;  // elements each lane carries per reservation round
 
 __device__ __forceinline__ bool in_pass(const BucketOut &B, unsigned b) { return b >= B.lo && b < B.hi; }
 
-// Elements past their bucket's region go to the overflow list: the lanes that
-// overflow in one round reserve their places with one atomic (every lane calls it).
-__device__ __forceinline__ void overflow_append(const BucketOut &B, bool of, const ulonglong2 &sl) {
+// Elements past their bucket's region go to the overflow list.  Each warp
+// takes the list in chunks of kOvfChunk places (one atomic on the list's
+// counter per chunk; the counter is shared by every warp of the GPU) and fills
+// them in order; the places a warp leaves unused are marked empty (key
+// kEmpty), which the sort by bucket skips.  cur = {next place, chunk end} in
+// the warp's shared memory.  Every lane calls it.
+constexpr unsigned kOvfChunk = 256;
+
+__device__ __forceinline__ void ovf_pad(const BucketOut &B, unsigned long long q, unsigned long long end) {
+    for (q += threadIdx.x & 31; q < end; q += 32)
+        if ((long long)q < B.ovf_cap) reinterpret_cast<ulonglong2 *>(B.ovf)[q] = make_ulonglong2(kEmpty, 0ull);
+}
+
+__device__ __forceinline__ void overflow_append(const BucketOut &B, bool of, const ulonglong2 &sl,
+                                                unsigned long long *cur) {
     const unsigned lane = threadIdx.x & 31;
     const unsigned bal = __ballot_sync(kFull, of);
     if (!bal) return;
-    const int leader = __ffs(bal) - 1;
-    unsigned long long q0 = 0;
-    if ((int)lane == leader) q0 = atomicAdd(B.ovf_n, (unsigned long long)__popc(bal));
-    q0 = __shfl_sync(kFull, q0, leader);
+    const unsigned n = __popc(bal);
+    unsigned long long pos = cur[0], end = cur[1];
+    if (pos + n > end) {
+        ovf_pad(B, pos, end);
+        unsigned long long q0 = 0;
+        if (lane == 0) q0 = atomicAdd(B.ovf_n, (unsigned long long)kOvfChunk);
+        pos = __shfl_sync(kFull, q0, 0);
+        end = pos + kOvfChunk;
+    }
+    __syncwarp();
+    if (lane == 0) cur[0] = pos + n, cur[1] = end;
+    __syncwarp();
     if (!of) return;
-    const unsigned long long q = q0 + __popc(bal & ((1u << lane) - 1u));
+    const unsigned long long q = pos + __popc(bal & ((1u << lane) - 1u));
     if ((long long)q < B.ovf_cap) reinterpret_cast<ulonglong2 *>(B.ovf)[q] = sl;
     else atomicOr(B.status, 2);
 }
@@ -155,7 +176,8 @@ __device__ __forceinline__ void overflow_append(const BucketOut &B, bool of, con
 // of the warp that share a bucket reserve their slots with one atomic, issued
 // for all k before any result is used, and write one run.
 __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, const unsigned *bk,
-                                            const unsigned long long *tg, const double *v) {
+                                            const unsigned long long *tg, const double *v,
+                                            unsigned long long *cur) {
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     unsigned peers[kU], base[kU];
 #pragma unroll
@@ -177,7 +199,7 @@ __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, 
             if (pos < o1 - o0) reinterpret_cast<ulonglong2 *>(B.elem)[o0 - B.base + pos] = sl;
             else of = true;
         }
-        overflow_append(B, of, sl);
+        overflow_append(B, of, sl, cur);
     }
 }
 
@@ -240,7 +262,8 @@ __device__ __forceinline__ bool row_wanted(const EmitOut &o, RowCtx rc, unsigned
 // A round whose elements all go to bucket b (a row with one bucket): one
 // reservation for the whole warp, positions by ballot prefix.
 __device__ __forceinline__ void single_append(const BucketOut &B, unsigned b, const bool *ok,
-                                              const unsigned long long *tg, const double *v) {
+                                              const unsigned long long *tg, const double *v,
+                                              unsigned long long *cur) {
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     unsigned pre[kU], tot = 0;
 #pragma unroll
@@ -264,7 +287,7 @@ __device__ __forceinline__ void single_append(const BucketOut &B, unsigned b, co
             if (pos < cap) dst[pos] = sl;
             else of = true;
         }
-        overflow_append(B, of, sl);
+        overflow_append(B, of, sl, cur);
     }
 }
 
@@ -294,7 +317,8 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
                                            const unsigned long long *ha, const unsigned long long *hb,
                                            const unsigned *bk, const double *e, const long long *di,
                                            long long s, double c, unsigned long long cb,
-                                           unsigned &inserted, long long single = -1) {
+                                           unsigned &inserted, unsigned long long *cur,
+                                           long long single = -1) {
     if constexpr (kMode == kModeDebug) {
 #pragma unroll
         for (int k = 0; k < kU; ++k)
@@ -325,8 +349,8 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
 #pragma unroll
             for (int k = 0; k < kU; ++k) ok[k] = ok[k] && !(fabs(v[k]) < o.b.eps_elem);
         }
-        if (single >= 0) single_append(o.b, (unsigned)single, ok, tg, v);
-        else warp_append(o.b, ok, bk, tg, v);
+        if (single >= 0) single_append(o.b, (unsigned)single, ok, tg, v, cur);
+        else warp_append(o.b, ok, bk, tg, v, cur);
     }
 }
 
@@ -384,7 +408,8 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wb = sm + block_smem(d) + size_t(warp) * warp_smem(d);
-    unsigned long long *rankA1 = reinterpret_cast<unsigned long long *>(wb);
+    unsigned long long *ocur = reinterpret_cast<unsigned long long *>(wb);  // overflow chunk cursor
+    unsigned long long *rankA1 = ocur + 2;
     unsigned long long *rankB1 = rankA1 + d.sa;
     unsigned long long *pre = rankB1 + d.sb;  // prefix sums A0 | A1 | A2, ks each
     unsigned long long *hopRC = pre + 3 * ks;  // bucket map entry of each kept alpha hop's row
@@ -404,6 +429,8 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     unsigned inserted = 0;
     const long long per = d.n_conn + 1;
+    if (lane == 0) ocur[0] = 0ull, ocur[1] = 0ull;
+    __syncwarp();
 
     for (long long s = gw; s < n_in; s += nw) {
         const unsigned long long r = in_rank[s];
@@ -499,7 +526,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     e[k] = flip(F, offA1[x] >> 31);
                 }
             }
-            emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted);
+            emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur);
         }
         long long off = base + 1 + d.sa;
         // beta singles (all in row hA)
@@ -516,7 +543,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     want[k] = true, ha[k] = hA, hb[k] = rankB1[y], di[k] = off + y;
                     e[k] = flip(F, offB1[y] >> 31);
                 }
-                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, self_single);
+                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, self_single);
             }
         }
         off += d.sb;
@@ -561,7 +588,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                                               : __dsub_rn(__ldg(&g[x1]), __ldg(&g[x2]));
                         e[k] = flip(gd, unsigned(s1 ^ s2));
                     }
-                    emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, spin ? self_single : -1);
+                    emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, spin ? self_single : -1);
                 }
                 __syncwarp();
             }
@@ -594,12 +621,16 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     cy += 32;
                     while (cy >= d.sb) cy -= d.sb, ++cx;
                 }
-                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted,
+                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur,
                                   kMode == kModeBucket ? round_single(want, bk) : -1);
             }
         }
 #undef SFCI_CLEAR
         __syncwarp();
+    }
+    if constexpr (kMode == kModeBucket) {  // the unused rest of the warp's overflow chunk
+        __syncwarp();
+        ovf_pad(o.b, ocur[0], ocur[1]);
     }
     if (kMode == kModeTable) {
         for (int w = 16; w > 0; w >>= 1) inserted += __shfl_xor_sync(kFull, inserted, w);

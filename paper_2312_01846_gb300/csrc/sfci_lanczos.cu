@@ -399,13 +399,14 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     double sig_need = std::min(16.0 * (double)z->nkeep, E) + 2.0 * (double)z->nkeep + 1024.0;
     // overflow list per pass: 1.5 times the most any pass of the previous sigma
     // needed, grown by (element ratio)^0.75 when the input grew (a larger input
-    // also runs more passes), at least 2^20 entries; a list that proves short
-    // is grown and the sigma redone
+    // also runs more passes), at least 2^22 entries (warps take it in chunks of
+    // 256 places); a pass that finds it short is split into pieces, or the
+    // sigma is redone with a longer list
     // (and at least what this basis index needed one cycle earlier: a cycle's
     // first vector, the restart, concentrates sigma and overflows most)
     const double at_i = i < (int)z->ovf_at.size() ? (double)z->ovf_at[i] : 0.0;
     long long ovf_cap = std::max<long long>(
-        1 << 20, (long long)(1.5 * std::max(at_i, (double)z->ovf_used *
+        1 << 22, (long long)(1.5 * std::max(at_i, (double)z->ovf_used *
                                                 std::pow(std::max(1.0, E / std::max(1.0, z->elem_prev)), 0.75))));
     long long totp = 0;
     for (int j = 0; j <= i; ++j) totp += z->wn[j];
@@ -505,6 +506,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         while ((1ull << z->nb_log2) < B) ++z->nb_log2;
         z->ms_emit = z->ms_merge = 0.0;
         unsigned long long max_ovf = 0;  // most overflow elements of any pass
+        unsigned long long ovf_short = 0;  // a range's overflow that the list could not hold
         z->n_split = 0;
         // passes as bucket ranges; a range whose overflow outgrew the list is
         // split in two and emitted again (its merge has not run yet)
@@ -547,28 +549,40 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             SFCI_CUDA(cudaEventRecord(z->evp[0], z->st));
             SFCI_CUDA(launch_emit_buckets(d, z->wr[i], z->wc[i], n_in, bo, z->st, z->p.emit_warps));
             SFCI_CUDA(cudaEventRecord(z->evp[1], z->st));
-            if (hi - lo > 1) {
-                unsigned long long on = 0;
-                SFCI_CUDA(cudaMemcpyAsync(&on, z->ovf_n, 8, cudaMemcpyDeviceToHost, z->st));
-                SFCI_CUDA(cudaStreamSynchronize(z->st));
-                if ((long long)on > z->ovf_cap) {
+            unsigned long long on = 0;
+            SFCI_CUDA(cudaMemcpyAsync(&on, z->ovf_n, 8, cudaMemcpyDeviceToHost, z->st));
+            SFCI_CUDA(cudaStreamSynchronize(z->st));
+            if ((long long)on > z->ovf_cap) {
+                float a = 0.f;
+                cudaEventElapsedTime(&a, z->evp[0], z->evp[1]);
+                z->ms_emit += a;
+                // the list was short for this range: split the range into pieces
+                // the list can hold (each re-emits over all sources) when that is
+                // cheaper than redoing sigma with a longer list
+                const double k_need = std::ceil(1.25 * (double)on / (double)z->ovf_cap);
+                if (hi - lo >= 2 && k_need <= 3.0 && z->n_split < 6) {
                     int hs2 = 0;
                     SFCI_CUDA(cudaMemcpyAsync(&hs2, z->mstatus, 4, cudaMemcpyDeviceToHost, z->st));
                     SFCI_CUDA(cudaStreamSynchronize(z->st));
-                    hs2 &= ~2;  // the list's truncation bit: this range is redone in halves
+                    hs2 &= ~2;  // the list's truncation bit: this range is emitted again in pieces
                     SFCI_CUDA(cudaMemcpyAsync(z->mstatus, &hs2, 4, cudaMemcpyHostToDevice, z->st));
                     SFCI_CUDA(cudaMemsetAsync(P<unsigned>(z->bcount) + lo, 0, size_t(hi - lo) * 4, z->st));
-                    unsigned mid = lo + 1;
-                    const unsigned long long half = (z->h_boff[lo] + z->h_boff[hi]) / 2;
-                    while (mid + 1 < hi && z->h_boff[mid] < half) ++mid;
-                    ranges.emplace_back(mid, hi);
-                    ranges.emplace_back(lo, mid);
-                    float a = 0.f;
-                    cudaEventElapsedTime(&a, z->evp[0], z->evp[1]);
-                    z->ms_emit += a;
-                    ++z->n_split;
+                    const unsigned k = std::min<unsigned>(hi - lo, (unsigned)k_need);
+                    std::vector<unsigned> cut{lo};
+                    const unsigned long long r0 = z->h_boff[lo], r1 = z->h_boff[hi];
+                    for (unsigned j = 1; j < k; ++j) {
+                        unsigned m = cut.back() + 1;
+                        const unsigned long long want_at = r0 + (r1 - r0) * j / k;
+                        while (m + (k - j) < hi && z->h_boff[m] < want_at) ++m;
+                        cut.push_back(m);
+                    }
+                    cut.push_back(hi);
+                    for (unsigned j = k; j > 0; --j) ranges.emplace_back(cut[j - 1], cut[j]);
+                    z->n_split += (int)k - 1;
                     continue;
                 }
+                ovf_short = std::max(ovf_short, on);
+                break;
             }
             SFCI_CUDA(sort_overflow(bk, P<unsigned>(z->bcount), lo, hi - lo, P<Slot>(z->bovf), z->ovf_n,
                                     z->ovf_cap, P<unsigned>(z->tmp_counts), P<unsigned long long>(z->ovf_off),
@@ -628,7 +642,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         SFCI_CUDA(cudaStreamSynchronize(z->st));
         std::memcpy(&tau, &tb, 8);  // as raised during the merge
         *tau_io = tau;
-        if (hs == 0) {
+        if (hs == 0 && !ovf_short) {
             *n_out = ho, *n_live = hl, *n_nonzero = hz, *sumsq = hq;
             z->stream_prev = ho;
             z->ovf_used = (long long)max_ovf;
@@ -647,8 +661,10 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             *tau_io = tau;
             continue;
         }
+        if (ovf_short) hs |= 2;  // passes left out: redo
         if (hs & 2) {  // the overflow list was cut short: the merge saw part of it, redo
-            ovf_cap *= 4;  // (from the threshold this attempt started with)
+            // (from the threshold this attempt started with)
+            ovf_cap = std::max(ovf_cap * 4, (long long)(1.5 * (double)ovf_short));
             tau = tau_start;
             *tau_io = tau;
             continue;

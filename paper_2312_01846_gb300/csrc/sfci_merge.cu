@@ -231,12 +231,13 @@ __global__ void ovf_scatter_kernel(Buckets bk, const Slot *ovf, const unsigned l
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
         const long long i = i0 + lane;
-        const bool act = i < n;
+        bool act = i < n;
         ulonglong2 e = make_ulonglong2(0ull, 0ull);
         unsigned b = 0;
         if (act) {
             e = reinterpret_cast<const ulonglong2 *>(ovf)[i];
-            b = bucket_key(bk, e.x) - lo;
+            act = e.x != kEmpty;  // a place the emitting warp left unused
+            if (act) b = bucket_key(bk, e.x) - lo;
         }
         const unsigned peers = __match_any_sync(kFull, act ? b : (0x80000000u | lane));
         const int leader = __ffs(peers) - 1;
