@@ -349,6 +349,10 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
 #pragma unroll
             for (int k = 0; k < kU; ++k) ok[k] = ok[k] && !(fabs(v[k]) < o.b.eps_elem);
         }
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < kU; ++k) any |= ok[k];
+        if (!__any_sync(kFull, any)) return;  // nothing of this pass in the round
         if (single >= 0) single_append(o.b, (unsigned)single, ok, tg, v, cur);
         else warp_append(o.b, ok, bk, tg, v, cur);
     }

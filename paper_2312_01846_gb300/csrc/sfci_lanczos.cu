@@ -425,18 +425,30 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if (z->p.mem_budget > 0) avail = std::min(avail, (double)z->p.mem_budget);
         const double budget = avail - 1.1 * sig_need * 16.0 - 3.0 * ovf_cap * 16.0;  // two overflow lists with 50 % headroom
         // passes: contiguous bucket ranges whose regions fit the budget
-        std::vector<unsigned long long> cuts{0};
+        std::vector<unsigned long long> cuts;
         unsigned long long max_pass = 0;
-        for (unsigned long long b = 0; b < B;) {
-            unsigned long long hi = b + 1;
-            while (hi < B && (double)(z->h_boff[hi + 1] - z->h_boff[b]) * sizeof(Slot) <= budget) ++hi;
-            if ((double)(z->h_boff[hi] - z->h_boff[b]) * sizeof(Slot) > budget) {
-                set_error("not enough device memory for one merge bucket");
-                return SFCI_E_CAPACITY;
+        auto plan_passes = [&](double bud, std::vector<unsigned long long> &cu, unsigned long long &mx) {
+            cu.assign(1, 0ull);
+            mx = 0;
+            for (unsigned long long b = 0; b < B;) {
+                unsigned long long hi = b + 1;
+                while (hi < B && (double)(z->h_boff[hi + 1] - z->h_boff[b]) * sizeof(Slot) <= bud) ++hi;
+                if ((double)(z->h_boff[hi] - z->h_boff[b]) * sizeof(Slot) > bud) return false;
+                mx = std::max(mx, z->h_boff[hi] - z->h_boff[b]);
+                cu.push_back(hi);
+                b = hi;
             }
-            max_pass = std::max(max_pass, z->h_boff[hi] - z->h_boff[b]);
-            cuts.push_back(hi);
-            b = hi;
+            return true;
+        };
+        if (!plan_passes(budget, cuts, max_pass)) {
+            set_error("not enough device memory for one merge bucket");
+            return SFCI_E_CAPACITY;
+        }
+        // the element regions already allocated serve when they give as few passes
+        if (z->belem.bytes > 0 && (double)z->belem.bytes < budget) {
+            std::vector<unsigned long long> c2;
+            unsigned long long m2 = 0;
+            if (plan_passes((double)z->belem.bytes, c2, m2) && c2.size() == cuts.size()) cuts.swap(c2), max_pass = m2;
         }
         const int npass = (int)cuts.size() - 1;
         const size_t want_elem = size_t(max_pass) * sizeof(Slot);
