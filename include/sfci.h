@@ -185,7 +185,12 @@ typedef struct sfci_params {
     int64_t mem_budget;     /* device bytes this solver's sigma buffers may take;
                                0 = 85 % of what is free (one solver per device)   */
     int32_t emit_warps;     /* warps per CTA of the element generator (1..8); 0 = 8 */
-    int32_t reserved;       /* pass 0                                                */
+    int32_t ovf_max_log2;   /* the overflow list (elements past their merge bucket's
+                               region) holds at most 2^ovf_max_log2 entries;
+                               0 = sized from free memory.  A pass whose overflow
+                               does not fit is split into pieces, or sigma is
+                               redone with a longer list (up to this limit);
+                               SFCI_E_CAPACITY when no attempt fits            */
     double eps_element;     /* heat-bath style selection (the outlook of Sec. 4):
                                intermediate elements with |<D'|H|D> c_D| <
                                eps_element are not generated, whole excitation

@@ -34,7 +34,7 @@ class Params(C.Structure):
                 ("eps_screen", C.c_double), ("conv_tol", C.c_double),
                 ("n_lanczos", C.c_int32), ("max_iter", C.c_int32),
                 ("flags", C.c_uint32), ("bucket_elems", C.c_int32),
-                ("mem_budget", C.c_int64), ("emit_warps", C.c_int32), ("reserved", C.c_int32),
+                ("mem_budget", C.c_int64), ("emit_warps", C.c_int32), ("ovf_max_log2", C.c_int32),
                 ("eps_element", C.c_double)]
 
 
@@ -325,13 +325,13 @@ class Lanczos:
 
     def __init__(self, sys: System, init_rank, init_coef, n_keep, n_lanczos=10, max_iter=0,
                  eps_screen=0.0, conv_tol=0.0, table_capacity=0, bucket_elems=0, stream=None,
-                 mem_budget=0, emit_warps=0, eps_element=0.0):
+                 mem_budget=0, emit_warps=0, eps_element=0.0, ovf_max_log2=0):
         self.sys = sys
         r = _dev(init_rank, torch.int64)
         c = _dev(init_coef, torch.float64)
         self.params = Params(int(n_keep), int(table_capacity), float(eps_screen), float(conv_tol),
                              int(n_lanczos), int(max_iter), 0, int(bucket_elems),
-                             int(mem_budget), int(emit_warps), 0, float(eps_element))
+                             int(mem_budget), int(emit_warps), int(ovf_max_log2), float(eps_element))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         _check(lib().sfci_lanczos_create(C.byref(h), sys.handle, C.byref(self.params), _ptr(r),

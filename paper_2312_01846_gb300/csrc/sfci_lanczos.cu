@@ -17,6 +17,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -405,9 +406,12 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     // (and at least what this basis index needed one cycle earlier: a cycle's
     // first vector, the restart, concentrates sigma and overflows most)
     const double at_i = i < (int)z->ovf_at.size() ? (double)z->ovf_at[i] : 0.0;
+    const long long ovf_lim = z->p.ovf_max_log2 > 0 ? 1ll << std::min(z->p.ovf_max_log2, 40)
+                                                    : std::numeric_limits<long long>::max();
     long long ovf_cap = std::max<long long>(
         1 << 22, (long long)(1.5 * std::max(at_i, (double)z->ovf_used *
                                                 std::pow(std::max(1.0, E / std::max(1.0, z->elem_prev)), 0.75))));
+    ovf_cap = std::min(ovf_cap, ovf_lim);
     long long totp = 0;
     for (int j = 0; j <= i; ++j) totp += z->wn[j];
     // fixed-point unit of the exact sums: sigma entries are bounded by
@@ -423,44 +427,45 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                             (double)z->bovf.bytes + (double)z->bovf_sorted.bytes;
         double avail = 0.85 * ((double)free_b + held);
         if (z->p.mem_budget > 0) avail = std::min(avail, (double)z->p.mem_budget);
-        const double budget = avail - 1.1 * sig_need * 16.0 - 3.0 * ovf_cap * 16.0;  // two overflow lists with 50 % headroom
-        // passes: contiguous bucket ranges whose regions fit the budget
+        const double sig_bytes = 1.1 * sig_need * 16.0;
+        const double budget = avail - sig_bytes - 2.0 * ovf_cap * 16.0;  // for the element regions
+        // passes: the fewest contiguous bucket ranges of about equal regions that
+        // fit the budget (cut where the running region total crosses j/npass)
+        const unsigned long long total_slots = z->h_boff[B];
         std::vector<unsigned long long> cuts;
         unsigned long long max_pass = 0;
-        auto plan_passes = [&](double bud, std::vector<unsigned long long> &cu, unsigned long long &mx) {
-            cu.assign(1, 0ull);
-            mx = 0;
-            for (unsigned long long b = 0; b < B;) {
-                unsigned long long hi = b + 1;
-                while (hi < B && (double)(z->h_boff[hi + 1] - z->h_boff[b]) * sizeof(Slot) <= bud) ++hi;
-                if ((double)(z->h_boff[hi] - z->h_boff[b]) * sizeof(Slot) > bud) return false;
-                mx = std::max(mx, z->h_boff[hi] - z->h_boff[b]);
-                cu.push_back(hi);
-                b = hi;
+        const int npass0 = std::max(1, (int)std::min(1e6, std::ceil((double)total_slots * sizeof(Slot) /
+                                                                   std::max(budget, 1.0))));
+        int npass = npass0;
+        for (;; ++npass) {
+            if (npass > (long long)B || budget <= 0.0 || npass > 4 * npass0 + 64) {
+                set_error("not enough device memory for one merge bucket");
+                return SFCI_E_CAPACITY;
             }
-            return true;
-        };
-        if (!plan_passes(budget, cuts, max_pass)) {
-            set_error("not enough device memory for one merge bucket");
-            return SFCI_E_CAPACITY;
+            cuts.assign(1, 0ull);
+            for (int j = 1; j < npass; ++j) {
+                const unsigned long long at = (unsigned long long)((double)total_slots * j / npass);
+                unsigned long long c = (unsigned long long)(std::lower_bound(z->h_boff.begin(), z->h_boff.begin() + B,
+                                                                             at) - z->h_boff.begin());
+                c = std::max(c, cuts.back() + 1);
+                c = std::min(c, B - (unsigned long long)(npass - j));
+                cuts.push_back(c);
+            }
+            cuts.push_back(B);
+            max_pass = 0;
+            for (int j = 0; j < npass; ++j) max_pass = std::max(max_pass, z->h_boff[cuts[j + 1]] - z->h_boff[cuts[j]]);
+            if ((double)max_pass * sizeof(Slot) <= budget) break;
         }
-        // the element regions already allocated serve when they give as few passes
-        if (z->belem.bytes > 0 && (double)z->belem.bytes < budget) {
-            std::vector<unsigned long long> c2;
-            unsigned long long m2 = 0;
-            if (plan_passes((double)z->belem.bytes, c2, m2) && c2.size() == cuts.size()) cuts.swap(c2), max_pass = m2;
-        }
-        const int npass = (int)cuts.size() - 1;
-        const size_t want_elem = size_t(max_pass) * sizeof(Slot);
+        const size_t need_elem = size_t(max_pass) * sizeof(Slot);
         size_t want_sig = size_t(sig_need) * 8;
         const auto t_alloc0 = std::chrono::steady_clock::now();
-        const size_t want_ovf = size_t(ovf_cap) * sizeof(Slot);
-        if (z->belem.bytes < want_elem || z->sig_key.bytes < want_sig || z->sig_val.bytes < want_sig ||
-            z->bovf.bytes < want_ovf || z->bovf_sorted.bytes < want_ovf ||
-            z->bovf.bytes > 8 * want_ovf + (size_t(4) << 30)) {
+        const size_t need_ovf = size_t(ovf_cap) * sizeof(Slot);
+        if (z->belem.bytes < need_elem || z->sig_key.bytes < want_sig || z->sig_val.bytes < want_sig ||
+            z->bovf.bytes < need_ovf || z->bovf_sorted.bytes < need_ovf) {
             // the large buffers (elements, stream, overflow lists) are sized together
-            // from one budget: free them all, then give the sigma output 10 % headroom
-            // out of the same budget
+            // from one budget: free them all; the element regions get 5 % headroom,
+            // the stream 10 %, and the overflow lists what is left (a longer list
+            // saves splitting passes), up to a fifth of the elements each
             SFCI_CUDA(cudaStreamSynchronize(z->st));
             for (auto *bb : {&z->belem, &z->sig_key, &z->sig_val, &z->bovf, &z->bovf_sorted}) {
                 cudaFree(bb->p);
@@ -468,17 +473,20 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                 bb->bytes = 0;
             }
             want_sig = size_t(1.1 * sig_need) * 8;
+            const size_t want_elem = size_t(std::min((double)need_elem * 1.05, budget));
+            const double left = avail - sig_bytes - (double)want_elem;
+            const double ovf_room = std::min({left / (2.0 * sizeof(Slot)), 0.2 * E + (double)(1 << 22),
+                                              (double)ovf_lim});
+            const size_t want_ovf = size_t(std::max((double)ovf_cap, ovf_room)) * sizeof(Slot);
+            if ((r = ensure(z->sig_key, want_sig, z->st, "sigma keys"))) return r;
+            if ((r = ensure(z->sig_val, want_sig, z->st, "sigma values"))) return r;
+            if ((r = ensure(z->bovf, want_ovf, z->st, "overflow list"))) return r;
+            if ((r = ensure(z->bovf_sorted, want_ovf, z->st, "sorted overflow"))) return r;
+            if ((r = ensure(z->belem, want_elem, z->st, "element regions"))) return r;
         }
-        if ((r = ensure(z->sig_key, want_sig, z->st, "sigma keys"))) return r;
-        if ((r = ensure(z->sig_val, want_sig, z->st, "sigma values"))) return r;
         z->sig_cap = (long long)(std::min(z->sig_key.bytes, z->sig_val.bytes) / 8);
-        // the overflow lists get 50 % headroom, so small changes in overflow
-        // do not reallocate the whole group
-        if ((r = ensure(z->bovf, want_ovf, z->st, "overflow list", 1.5))) return r;
-        if ((r = ensure(z->bovf_sorted, want_ovf, z->st, "sorted overflow", 1.5))) return r;
-        ovf_cap = (long long)(std::min(z->bovf.bytes, z->bovf_sorted.bytes) / sizeof(Slot));
+        ovf_cap = std::min((long long)(std::min(z->bovf.bytes, z->bovf_sorted.bytes) / sizeof(Slot)), ovf_lim);
         z->ovf_cap = ovf_cap;
-        if ((r = ensure(z->belem, want_elem, z->st, "element regions"))) return r;
         if ((r = ensure(z->bcount, size_t(B) * 4, z->st, "bucket counters", 1.5))) return r;
         if ((r = ensure(z->probes, size_t(std::max<long long>(totp, 1)) * sizeof(Probe), z->st, "probes"))) return r;
         if ((r = ensure(z->pcount, size_t(B) * 4, z->st, "probe counts", 1.5))) return r;
@@ -571,15 +579,17 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                 // the list was short for this range: split the range into pieces
                 // the list can hold (each re-emits over all sources) when that is
                 // cheaper than redoing sigma with a longer list
+                // (when the list is at its limit, splitting is the only way on)
                 const double k_need = std::ceil(1.25 * (double)on / (double)z->ovf_cap);
-                if (hi - lo >= 2 && k_need <= 3.0 && z->n_split < 6) {
+                const bool can_grow = z->ovf_cap < ovf_lim;
+                const unsigned k = (unsigned)std::min<double>(hi - lo, k_need);
+                if (hi - lo >= 2 && (k_need <= 3.0 || !can_grow) && z->n_split + (int)k - 1 <= (can_grow ? 6 : 64)) {
                     int hs2 = 0;
                     SFCI_CUDA(cudaMemcpyAsync(&hs2, z->mstatus, 4, cudaMemcpyDeviceToHost, z->st));
                     SFCI_CUDA(cudaStreamSynchronize(z->st));
                     hs2 &= ~2;  // the list's truncation bit: this range is emitted again in pieces
                     SFCI_CUDA(cudaMemcpyAsync(z->mstatus, &hs2, 4, cudaMemcpyHostToDevice, z->st));
                     SFCI_CUDA(cudaMemsetAsync(P<unsigned>(z->bcount) + lo, 0, size_t(hi - lo) * 4, z->st));
-                    const unsigned k = std::min<unsigned>(hi - lo, (unsigned)k_need);
                     std::vector<unsigned> cut{lo};
                     const unsigned long long r0 = z->h_boff[lo], r1 = z->h_boff[hi];
                     for (unsigned j = 1; j < k; ++j) {
@@ -676,7 +686,12 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if (ovf_short) hs |= 2;  // passes left out: redo
         if (hs & 2) {  // the overflow list was cut short: the merge saw part of it, redo
             // (from the threshold this attempt started with)
-            ovf_cap = std::max(ovf_cap * 4, (long long)(1.5 * (double)ovf_short));
+            const long long grown = std::min(std::max(ovf_cap * 4, (long long)(1.5 * (double)ovf_short)), ovf_lim);
+            if (grown <= ovf_cap) {
+                set_error("the overflow list (elements past their merge bucket's region) needs more than its limit");
+                return SFCI_E_CAPACITY;
+            }
+            ovf_cap = grown;
             tau = tau_start;
             *tau_io = tau;
             continue;
