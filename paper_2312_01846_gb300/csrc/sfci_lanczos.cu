@@ -583,7 +583,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                 const double k_need = std::ceil(1.25 * (double)on / (double)z->ovf_cap);
                 const bool can_grow = z->ovf_cap < ovf_lim;
                 const unsigned k = (unsigned)std::min<double>(hi - lo, k_need);
-                if (hi - lo >= 2 && (k_need <= 3.0 || !can_grow) && z->n_split + (int)k - 1 <= (can_grow ? 6 : 64)) {
+                if (hi - lo >= 2 && (k_need <= 3.0 || !can_grow) && z->n_split + (int)k - 1 <= (can_grow ? 6 : 256)) {
                     int hs2 = 0;
                     SFCI_CUDA(cudaMemcpyAsync(&hs2, z->mstatus, 4, cudaMemcpyDeviceToHost, z->st));
                     SFCI_CUDA(cudaStreamSynchronize(z->st));
