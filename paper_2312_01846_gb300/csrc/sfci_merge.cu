@@ -346,7 +346,7 @@ __device__ __noinline__ void raise_threshold(const MergeArgs &A, int tid, int *s
 }
 
 template <int kSlots>
-__global__ void __launch_bounds__(kMT)
+__global__ void __launch_bounds__(kMT, 4)
 merge_kernel(MergeArgs A) {
     extern __shared__ __align__(16) unsigned char msm[];
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(msm);
@@ -396,7 +396,25 @@ merge_kernel(MergeArgs A) {
             for (int k = 0; k < kPre; ++k) {
                 if (e0 + (unsigned)k * kMT >= total) break;  // block-uniform: no elements left
                 const unsigned long long key = x[k].x;
-                const bool act = key != kEmpty;
+                // lanes holding the same key: the lowest one sums the group's
+                // values (exact integer adds) and alone touches the table, so a
+                // key that many elements share costs one atomic per warp round
+                const unsigned peers = __match_any_sync(kFull, key);
+                const bool act = key != kEmpty && (peers & lt) == 0;
+                Fix128 f{0ull, 0ull};
+                if (key != kEmpty) f = to_fixed(__longlong_as_double((long long)x[k].y), S, range_ok);
+                const Fix128 f0 = f;
+                unsigned todo = act ? peers & ~(1u << lane) : 0u;
+                while (__any_sync(kFull, todo != 0u)) {
+                    const int src = todo ? __ffs(todo) - 1 : lane;
+                    const unsigned long long olo = __shfl_sync(kFull, f0.lo, src);
+                    const unsigned long long ohi = __shfl_sync(kFull, f0.hi, src);
+                    if (todo) {
+                        f.lo += olo;
+                        f.hi += ohi + (f.lo < olo ? 1ull : 0ull);
+                        todo &= todo - 1u;
+                    }
+                }
                 unsigned h = 0;
                 bool ins = false, found = false;
                 if (act) {
@@ -429,7 +447,6 @@ merge_kernel(MergeArgs A) {
                 }
                 if (act) {
                     if (found) {
-                        const Fix128 f = to_fixed(__longlong_as_double((long long)x[k].y), S, range_ok);
                         const unsigned long long old = atomicAdd(&acc_lo[h], f.lo);
                         atomicAdd(&acc_hi[h], f.hi + (old + f.lo < old ? 1ull : 0ull));  // with the carry
                     } else {
