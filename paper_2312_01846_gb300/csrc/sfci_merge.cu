@@ -383,6 +383,8 @@ merge_kernel(MergeArgs A) {
         const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(A.elem) + (r0 - A.bk.boff[A.lo]);
         const ulonglong2 *ovs = reinterpret_cast<const ulonglong2 *>(A.ovf_sorted) + o0;
         const unsigned total = n_main + (unsigned)(o1 - o0);
+        // a bucket past its region holds keys that many sources reach
+        const bool hot = o1 > o0;
         for (unsigned e0 = 0; e0 < total; e0 += kMT * kPre) {
             ulonglong2 x[kPre];
 #pragma unroll
@@ -396,23 +398,26 @@ merge_kernel(MergeArgs A) {
             for (int k = 0; k < kPre; ++k) {
                 if (e0 + (unsigned)k * kMT >= total) break;  // block-uniform: no elements left
                 const unsigned long long key = x[k].x;
-                // lanes holding the same key: the lowest one sums the group's
-                // values (exact integer adds) and alone touches the table, so a
-                // key that many elements share costs one atomic per warp round
-                const unsigned peers = __match_any_sync(kFull, key);
-                const bool act = key != kEmpty && (peers & lt) == 0;
                 Fix128 f{0ull, 0ull};
                 if (key != kEmpty) f = to_fixed(__longlong_as_double((long long)x[k].y), S, range_ok);
-                const Fix128 f0 = f;
-                unsigned todo = act ? peers & ~(1u << lane) : 0u;
-                while (__any_sync(kFull, todo != 0u)) {
-                    const int src = todo ? __ffs(todo) - 1 : lane;
-                    const unsigned long long olo = __shfl_sync(kFull, f0.lo, src);
-                    const unsigned long long ohi = __shfl_sync(kFull, f0.hi, src);
-                    if (todo) {
-                        f.lo += olo;
-                        f.hi += ohi + (f.lo < olo ? 1ull : 0ull);
-                        todo &= todo - 1u;
+                bool act = key != kEmpty;
+                if (hot) {
+                    // lanes holding the same key: the lowest one sums the group's
+                    // values (exact integer adds) and alone touches the table, so
+                    // a key that many elements share costs one atomic per round
+                    const unsigned peers = __match_any_sync(kFull, key);
+                    act = act && (peers & lt) == 0;
+                    const Fix128 f0 = f;
+                    unsigned todo = act ? peers & ~(1u << lane) : 0u;
+                    while (__any_sync(kFull, todo != 0u)) {
+                        const int src = todo ? __ffs(todo) - 1 : lane;
+                        const unsigned long long olo = __shfl_sync(kFull, f0.lo, src);
+                        const unsigned long long ohi = __shfl_sync(kFull, f0.hi, src);
+                        if (todo) {
+                            f.lo += olo;
+                            f.hi += ohi + (f.lo < olo ? 1ull : 0ull);
+                            todo &= todo - 1u;
+                        }
                     }
                 }
                 unsigned h = 0;
