@@ -35,13 +35,11 @@ __host__ __device__ inline size_t block_smem(const SysDev &d) {
     return align16(size_t(d.n + 1) * d.ks * 8) + align16(size_t(d.n_pairs) * 2);
 }
 
-// per warp: overflow chunk cursor (2 u64), full-bucket cache (kFullCache u32),
-// rankA1, rankB1 (u64), prefix sums (3 ks u64), hopRC (u64 per alpha hop),
-// offA1, offB1 (u32), hopX (u16 per alpha hop), occupation lists (256 B)
-constexpr int kFullCache = 64;
+// per warp: overflow chunk cursor (2 u64), rankA1, rankB1 (u64), prefix sums
+// (3 ks u64), hopRC (u64 per alpha hop), offA1, offB1 (u32), hopX (u16 per
+// alpha hop), occupation lists (256 B)
 __host__ __device__ inline size_t warp_smem(const SysDev &d) {
-    return align16(16 + kFullCache * 4 + size_t(d.sa + d.sb) * 12 + size_t(d.sa) * 10 + size_t(3 * d.ks) * 8 +
-                   256);
+    return align16(16 + size_t(d.sa + d.sb) * 12 + size_t(d.sa) * 10 + size_t(3 * d.ks) * 8 + 256);
 }
 
 inline size_t emit_smem_bytes_w(const SysDev &d, int warps) {
@@ -179,20 +177,15 @@ __device__ __forceinline__ void overflow_append(const BucketOut &B, bool of, con
 // for all k before any result is used, and write one run.
 __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, const unsigned *bk,
                                             const unsigned long long *tg, const double *v,
-                                            unsigned long long *cur, unsigned *full) {
+                                            unsigned long long *cur) {
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     unsigned peers[kU], base[kU];
-    bool direct[kU];  // bucket known to be full: straight to the overflow list
 #pragma unroll
-    for (int k = 0; k < kU; ++k) direct[k] = ok[k] && full[bk[k] & (kFullCache - 1)] == bk[k];
-#pragma unroll
-    for (int k = 0; k < kU; ++k)
-        peers[k] = __match_any_sync(kFull, ok[k] && !direct[k] ? bk[k] : (0x80000000u | lane));
+    for (int k = 0; k < kU; ++k) peers[k] = __match_any_sync(kFull, ok[k] ? bk[k] : (0x80000000u | lane));
 #pragma unroll
     for (int k = 0; k < kU; ++k) {
         base[k] = 0;
-        if (ok[k] && !direct[k] && (peers[k] & lt) == 0)
-            base[k] = atomicAdd(&B.count[bk[k]], (unsigned)__popc(peers[k]));
+        if (ok[k] && (peers[k] & lt) == 0) base[k] = atomicAdd(&B.count[bk[k]], (unsigned)__popc(peers[k]));
     }
 #pragma unroll
     for (int k = 0; k < kU; ++k) base[k] = __shfl_sync(kFull, base[k], __ffs(peers[k]) - 1);
@@ -200,17 +193,13 @@ __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, 
     for (int k = 0; k < kU; ++k) {
         bool of = false;
         const ulonglong2 sl = make_ulonglong2(tg[k], (unsigned long long)__double_as_longlong(v[k]));
-        if (ok[k] && !direct[k]) {
+        if (ok[k]) {
             const unsigned pos = base[k] + __popc(peers[k] & lt);
             const unsigned long long o0 = __ldg(&B.bk.boff[bk[k]]), o1 = __ldg(&B.bk.boff[bk[k] + 1]);
-            if (pos < o1 - o0) {
-                reinterpret_cast<ulonglong2 *>(B.elem)[o0 - B.base + pos] = sl;
-            } else {
-                of = true;
-                full[bk[k] & (kFullCache - 1)] = bk[k];  // later elements skip the counter
-            }
+            if (pos < o1 - o0) reinterpret_cast<ulonglong2 *>(B.elem)[o0 - B.base + pos] = sl;
+            else of = true;
         }
-        overflow_append(B, of || direct[k], sl, cur);
+        overflow_append(B, of, sl, cur);
     }
 }
 
@@ -274,7 +263,7 @@ __device__ __forceinline__ bool row_wanted(const EmitOut &o, RowCtx rc, unsigned
 // reservation for the whole warp, positions by ballot prefix.
 __device__ __forceinline__ void single_append(const BucketOut &B, unsigned b, const bool *ok,
                                               const unsigned long long *tg, const double *v,
-                                              unsigned long long *cur, unsigned *full) {
+                                              unsigned long long *cur) {
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     unsigned pre[kU], tot = 0;
 #pragma unroll
@@ -284,20 +273,18 @@ __device__ __forceinline__ void single_append(const BucketOut &B, unsigned b, co
         tot += __popc(bal);
     }
     if (tot == 0) return;
-    const bool direct = __shfl_sync(kFull, full[b & (kFullCache - 1)] == b, 0);  // lane 0's view for all
     unsigned base = 0;
-    if (!direct && lane == 0) base = atomicAdd(&B.count[b], tot);
+    if (lane == 0) base = atomicAdd(&B.count[b], tot);
     base = __shfl_sync(kFull, base, 0);
     const unsigned long long o0 = __ldg(&B.bk.boff[b]), cap = __ldg(&B.bk.boff[b + 1]) - o0;
     ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(B.elem) + (o0 - B.base);
-    if (!direct && base + tot > cap && lane == 0) full[b & (kFullCache - 1)] = b;
 #pragma unroll
     for (int k = 0; k < kU; ++k) {
         bool of = false;
         const ulonglong2 sl = make_ulonglong2(tg[k], (unsigned long long)__double_as_longlong(v[k]));
         if (ok[k]) {
             const unsigned pos = base + pre[k];
-            if (!direct && pos < cap) dst[pos] = sl;
+            if (pos < cap) dst[pos] = sl;
             else of = true;
         }
         overflow_append(B, of, sl, cur);
@@ -330,7 +317,7 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
                                            const unsigned long long *ha, const unsigned long long *hb,
                                            const unsigned *bk, const double *e, const long long *di,
                                            long long s, double c, unsigned long long cb,
-                                           unsigned &inserted, unsigned long long *cur, unsigned *full,
+                                           unsigned &inserted, unsigned long long *cur,
                                            long long single = -1) {
     if constexpr (kMode == kModeDebug) {
 #pragma unroll
@@ -366,8 +353,8 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
 #pragma unroll
         for (int k = 0; k < kU; ++k) any |= ok[k];
         if (!__any_sync(kFull, any)) return;  // nothing of this pass in the round
-        if (single >= 0) single_append(o.b, (unsigned)single, ok, tg, v, cur, full);
-        else warp_append(o.b, ok, bk, tg, v, cur, full);
+        if (single >= 0) single_append(o.b, (unsigned)single, ok, tg, v, cur);
+        else warp_append(o.b, ok, bk, tg, v, cur);
     }
 }
 
@@ -426,8 +413,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wb = sm + block_smem(d) + size_t(warp) * warp_smem(d);
     unsigned long long *ocur = reinterpret_cast<unsigned long long *>(wb);  // overflow chunk cursor
-    unsigned *ofull = reinterpret_cast<unsigned *>(ocur + 2);  // buckets this warp found full
-    unsigned long long *rankA1 = reinterpret_cast<unsigned long long *>(ofull + kFullCache);
+    unsigned long long *rankA1 = ocur + 2;
     unsigned long long *rankB1 = rankA1 + d.sa;
     unsigned long long *pre = rankB1 + d.sb;  // prefix sums A0 | A1 | A2, ks each
     unsigned long long *hopRC = pre + 3 * ks;  // bucket map entry of each kept alpha hop's row
@@ -448,7 +434,6 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
     unsigned inserted = 0;
     const long long per = d.n_conn + 1;
     if (lane == 0) ocur[0] = 0ull, ocur[1] = 0ull;
-    for (int t = lane; t < kFullCache; t += 32) ofull[t] = kNoBucket;
     __syncwarp();
 
     for (long long s = gw; s < n_in; s += nw) {
@@ -545,7 +530,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     e[k] = flip(F, offA1[x] >> 31);
                 }
             }
-            emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, ofull);
+            emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur);
         }
         long long off = base + 1 + d.sa;
         // beta singles (all in row hA)
@@ -562,7 +547,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     want[k] = true, ha[k] = hA, hb[k] = rankB1[y], di[k] = off + y;
                     e[k] = flip(F, offB1[y] >> 31);
                 }
-                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, ofull, self_single);
+                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, self_single);
             }
         }
         off += d.sb;
@@ -607,7 +592,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                                               : __dsub_rn(__ldg(&g[x1]), __ldg(&g[x2]));
                         e[k] = flip(gd, unsigned(s1 ^ s2));
                     }
-                    emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, ofull, spin ? self_single : -1);
+                    emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, spin ? self_single : -1);
                 }
                 __syncwarp();
             }
@@ -640,7 +625,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     cy += 32;
                     while (cy >= d.sb) cy -= d.sb, ++cx;
                 }
-                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, ofull,
+                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur,
                                   kMode == kModeBucket ? round_single(want, bk) : -1);
             }
         }

@@ -209,26 +209,14 @@ __global__ void scan_block_kernel(const unsigned *in, long long m, const unsigne
 
 // ------------------------------------------------------------- overflow
 
-// overflow elements per bucket of the pass, counted from the list (elements
-// of a bucket the emitting warp knew to be full skipped its counter); the
-// lanes of a warp that share a bucket add with one atomic
-__global__ void ovf_count_list_kernel(Buckets bk, const Slot *ovf, const unsigned long long *ovf_n,
-                                      long long ovf_cap, unsigned lo, unsigned *ovc) {
-    long long n = (long long)*ovf_n;
-    if (n > ovf_cap) n = ovf_cap;
-    const unsigned lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
-        const long long i = i0 + lane;
-        bool act = i < n;
-        unsigned b = 0;
-        if (act) {
-            const unsigned long long key = reinterpret_cast<const ulonglong2 *>(ovf)[i].x;
-            act = key != kEmpty;
-            if (act) b = bucket_key(bk, key) - lo;
-        }
-        const unsigned peers = __match_any_sync(kFull, act ? b : (0x80000000u | lane));
-        if (act && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&ovc[b], (unsigned)__popc(peers));
+// overflow elements per bucket of the pass = max(count - capacity, 0)
+__global__ void ovf_counts_kernel(const unsigned long long *boff, const unsigned *count, unsigned lo,
+                                  unsigned nb, unsigned *ovc) {
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+         b += (long long)gridDim.x * blockDim.x) {
+        const unsigned c = count[lo + b];
+        const unsigned cap = (unsigned)(boff[lo + b + 1] - boff[lo + b]);
+        ovc[b] = c > cap ? c - cap : 0u;
     }
 }
 
@@ -395,6 +383,8 @@ merge_kernel(MergeArgs A) {
         const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(A.elem) + (r0 - A.bk.boff[A.lo]);
         const ulonglong2 *ovs = reinterpret_cast<const ulonglong2 *>(A.ovf_sorted) + o0;
         const unsigned total = n_main + (unsigned)(o1 - o0);
+        // a bucket past its region holds keys that many sources reach
+        const bool hot = o1 > o0;
         for (unsigned e0 = 0; e0 < total; e0 += kMT * kPre) {
             ulonglong2 x[kPre];
 #pragma unroll
@@ -410,15 +400,15 @@ merge_kernel(MergeArgs A) {
                 const unsigned long long key = x[k].x;
                 Fix128 f{0ull, 0ull};
                 if (key != kEmpty) f = to_fixed(__longlong_as_double((long long)x[k].y), S, range_ok);
-                // four or more lanes holding the same key: the lowest one sums the
-                // group's values (exact integer adds) and alone touches the table,
-                // so a key that many elements share costs one atomic per round
-                const unsigned peers = __match_any_sync(kFull, key);
-                const bool big = key != kEmpty && __popc(peers) >= 4;
-                const bool act = key != kEmpty && (!big || (peers & lt) == 0);
-                if (__any_sync(kFull, big)) {
+                bool act = key != kEmpty;
+                if (hot) {
+                    // lanes holding the same key: the lowest one sums the group's
+                    // values (exact integer adds) and alone touches the table, so
+                    // a key that many elements share costs one atomic per round
+                    const unsigned peers = __match_any_sync(kFull, key);
+                    act = act && (peers & lt) == 0;
                     const Fix128 f0 = f;
-                    unsigned todo = big && act ? peers & ~(1u << lane) : 0u;
+                    unsigned todo = act ? peers & ~(1u << lane) : 0u;
                     while (__any_sync(kFull, todo != 0u)) {
                         const int src = todo ? __ffs(todo) - 1 : lane;
                         const unsigned long long olo = __shfl_sync(kFull, f0.lo, src);
@@ -707,13 +697,9 @@ cudaError_t sort_overflow(const Buckets &bk, const unsigned *count, unsigned lo,
                           const Slot *ovf, const unsigned long long *ovf_n, long long ovf_cap,
                           unsigned *tmp_counts, unsigned long long *off, void *scan_ws, Slot *out,
                           cudaStream_t st) {
-    (void)count;
-    cudaError_t e = cudaMemsetAsync(tmp_counts, 0, size_t(nb) * 4, st);
-    if (e != cudaSuccess) return e;
     count_launch();
-    ovf_count_list_kernel<<<grid_for(ovf_cap < (1 << 24) ? ovf_cap : (1 << 24), 8), 256, 0, st>>>(
-        bk, ovf, ovf_n, ovf_cap, lo, tmp_counts);
-    e = exclusive_scan(tmp_counts, nb, off, scan_ws, st);
+    ovf_counts_kernel<<<grid_for(nb, 8), 256, 0, st>>>(bk.boff, count, lo, nb, tmp_counts);
+    cudaError_t e = exclusive_scan(tmp_counts, nb, off, scan_ws, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(tmp_counts, 0, size_t(nb) * 4, st);
     if (e != cudaSuccess) return e;
