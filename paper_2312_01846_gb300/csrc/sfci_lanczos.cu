@@ -178,9 +178,8 @@ struct sfci_lanczos {
         size_t bytes = 0;
     };
     Buf bcount, belem, bovf, bovf_sorted, tmp_counts, ovf_off, probes, pcount, poff, scan_ws,
-        sig_key, sig_val, cand_key, cand_val, weights, rowmap, boff;
-    std::vector<unsigned long long> h_weights, h_map, h_boff;
-    std::vector<unsigned long long> h_nzrow, h_nzmap;  // rows with buckets and their map entries
+        sig_key, sig_val, cand_key, cand_val, weights, rowmap, boff,
+        wpre, ptl, pth, pbstart, pcap, pq;  // device bucket plan (row mode)
     long long sig_cap = 0, ovf_cap = 0, cand_cap = 0;
     double *sigw[kMaxVec] = {};
     char *words = nullptr;  // hist[kHistBins] | outn | mlive | ovf_n | cand_n | msumsq | queue | mstatus | nnz | dmin | tau | mark | lock
@@ -213,7 +212,8 @@ void destroy_lz(sfci_lanczos *z) {
     cudaFree(z->scratch);
     for (auto *b : {&z->bcount, &z->belem, &z->bovf, &z->bovf_sorted, &z->tmp_counts, &z->ovf_off,
                     &z->probes, &z->pcount, &z->poff, &z->scan_ws, &z->sig_key, &z->sig_val,
-                    &z->cand_key, &z->cand_val, &z->weights, &z->rowmap, &z->boff})
+                    &z->cand_key, &z->cand_val, &z->weights, &z->rowmap, &z->boff, &z->wpre, &z->ptl,
+                    &z->pth, &z->pbstart, &z->pcap, &z->pq})
         cudaFree(b->p);
     cudaFree(z->words);
     for (int j = 0; j < kMaxVec; ++j) cudaFree(z->sigw[j]);
@@ -323,62 +323,51 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     bk.cb = d.cb;
     unsigned long long B = 0;
     unsigned hash_cap = 0;
+    unsigned long long total_cap = 0;
     if (row_mode) {
-        // exact element count per target alpha string, then light rows packed
-        // into buckets of ~per_bucket elements and heavy rows split
+        // exact element count per target alpha string, then the bucket plan on
+        // the device: light rows packed into windows of half a bucket, heavy
+        // rows split into buckets of their own (sfci_plan.cu)
         const unsigned long long nrows = d.ca;
+        const unsigned long long Pb = std::max<unsigned long long>(2, (unsigned long long)per_bucket);
+        const unsigned long long T = (unsigned long long)(E / (double)(Pb / 2)) + 2;  // windows
         if ((r = ensure(z->weights, nrows * 8, z->st, "row weights", 1.5))) return r;
         if ((r = ensure(z->rowmap, nrows * 8, z->st, "row map", 1.5))) return r;
+        if ((r = ensure(z->wpre, (nrows + 1) * 8, z->st, "row offsets", 1.5))) return r;
+        if ((r = ensure(z->ptl, T * 4, z->st, "plan windows", 1.5))) return r;
+        if ((r = ensure(z->pth, T * 4, z->st, "plan windows", 1.5))) return r;
+        if ((r = ensure(z->pbstart, (T + 1) * 8, z->st, "plan window offsets", 1.5))) return r;
+        if ((r = ensure(z->scan_ws, scan_ws_bytes((long long)std::max(T, nrows) + 1), z->st, "scan workspace", 1.5)))
+            return r;
         SFCI_CUDA(cudaMemsetAsync(z->weights.p, 0, nrows * 8, z->st));
         SFCI_CUDA(launch_row_weights(d, z->wr[i], z->wc[i], n_in, z->p.eps_element,
                                      static_cast<unsigned long long *>(z->weights.p), z->st));
-        z->h_weights.resize(nrows);
-        SFCI_CUDA(cudaMemcpyAsync(z->h_weights.data(), z->weights.p, nrows * 8, cudaMemcpyDeviceToHost, z->st));
+        auto *w = P<unsigned long long>(z->weights);
+        SFCI_CUDA(exclusive_scan(static_cast<const unsigned long long *>(w), (long long)nrows,
+                                 P<unsigned long long>(z->wpre), z->scan_ws.p, z->st));
+        // windows: light flag in ptl, heavy bucket count in pth, their sum back in pth
+        SFCI_CUDA(plan_windows(w, P<unsigned long long>(z->wpre), nrows, Pb, T, P<unsigned>(z->ptl),
+                               P<unsigned>(z->pth), P<unsigned>(z->pth), z->st));
+        SFCI_CUDA(exclusive_scan(static_cast<const unsigned *>(P<unsigned>(z->pth)), (long long)T,
+                                 P<unsigned long long>(z->pbstart), z->scan_ws.p, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(&B, P<unsigned long long>(z->pbstart) + T, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaStreamSynchronize(z->st));
-        z->h_map.assign(nrows, 0ull);
-        std::vector<unsigned long long> caps;
-        caps.reserve(size_t(E / per_bucket) + 16);
-        bool open = false;
-        double acc = 0.0;
-        for (unsigned long long row = 0; row < nrows; ++row) {
-            const unsigned long long w = z->h_weights[row];
-            if (!w) continue;
-            if ((double)w > per_bucket) {
-                const unsigned long long ns = (unsigned long long)std::ceil((double)w / per_bucket);
-                // the beta hash splits w elements over ns buckets: mean w/ns, and
-                // four standard deviations of slack (the rest spills to the overflow list)
-                const double mu = (double)w / (double)ns;
-                const unsigned long long per = (unsigned long long)std::ceil(mu + 4.0 * std::sqrt(mu) + 32.0);
-                z->h_map[row] = ((unsigned long long)caps.size() << 32) | ns;
-                caps.insert(caps.end(), ns, per);
-                open = false;
-                continue;
-            }
-            if (!open || acc + (double)w > per_bucket) {
-                caps.push_back(0);
-                acc = 0.0;
-                open = true;
-            }
-            caps.back() += w;
-            acc += (double)w;
-            z->h_map[row] = ((unsigned long long)(caps.size() - 1) << 32) | 1ull;
-        }
-        // rows with buckets, in row (and bucket) order, for the pass row ranges
-        z->h_nzrow.clear();
-        z->h_nzmap.clear();
-        for (unsigned long long row = 0; row < nrows; ++row)
-            if (z->h_map[row]) z->h_nzrow.push_back(row), z->h_nzmap.push_back(z->h_map[row]);
-        B = caps.size();
         if (B >= (1ull << 31)) {
             set_error("too many merge buckets");
             return SFCI_E_CAPACITY;
         }
-        z->h_boff.resize(B + 1);
-        z->h_boff[0] = 0;
-        for (unsigned long long b = 0; b < B; ++b) z->h_boff[b + 1] = z->h_boff[b] + caps[b];
+        if ((r = ensure(z->pcap, std::max<unsigned long long>(B, 1) * 4, z->st, "bucket capacities", 1.5))) return r;
         if ((r = ensure(z->boff, (B + 1) * 8, z->st, "bucket offsets", 1.5))) return r;
-        SFCI_CUDA(cudaMemcpyAsync(z->rowmap.p, z->h_map.data(), nrows * 8, cudaMemcpyHostToDevice, z->st));
-        SFCI_CUDA(cudaMemcpyAsync(z->boff.p, z->h_boff.data(), (B + 1) * 8, cudaMemcpyHostToDevice, z->st));
+        if ((r = ensure(z->scan_ws, scan_ws_bytes((long long)std::max({T, nrows, B}) + 1), z->st, "scan workspace",
+                        1.5)))
+            return r;
+        SFCI_CUDA(plan_rows(w, P<unsigned long long>(z->wpre), nrows, Pb, P<unsigned>(z->ptl),
+                            P<unsigned long long>(z->pbstart), B, P<unsigned long long>(z->rowmap),
+                            P<unsigned>(z->pcap), z->st));
+        SFCI_CUDA(exclusive_scan(static_cast<const unsigned *>(P<unsigned>(z->pcap)), (long long)B,
+                                 P<unsigned long long>(z->boff), z->scan_ws.p, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(&total_cap, P<unsigned long long>(z->boff) + B, 8, cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaStreamSynchronize(z->st));
         bk.rowmap = static_cast<const unsigned long long *>(z->rowmap.p);
         bk.log2B = 0;
     } else {
@@ -388,12 +377,51 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         hash_cap = (unsigned)(std::ceil(1.125 * E / (double)B) + 128.0) & ~7u;
         if ((r = ensure(z->boff, (B + 1) * 8, z->st, "bucket offsets", 1.5))) return r;
         SFCI_CUDA(uniform_offsets(static_cast<unsigned long long *>(z->boff.p), B, hash_cap, z->st));
-        z->h_boff.resize(B + 1);
-        for (unsigned long long b = 0; b <= B; ++b) z->h_boff[b] = b * hash_cap;
         bk.log2B = log2B;
+        total_cap = B * (unsigned long long)hash_cap;
     }
     bk.boff = static_cast<const unsigned long long *>(z->boff.p);
-    const unsigned long long total_cap = z->h_boff[B];
+    // bucket offsets on the host side: first bucket at or above each target
+    // offset (and the offset there), and the offset of given buckets
+    auto lower_bounds = [&](const std::vector<unsigned long long> &tg, std::vector<unsigned long long> &idx,
+                            std::vector<unsigned long long> &at) -> cudaError_t {
+        const size_t n = tg.size();
+        idx.assign(n, 0ull);
+        at.assign(n, 0ull);
+        if (!n) return cudaSuccess;
+        if (!row_mode) {
+            for (size_t k = 0; k < n; ++k) {
+                idx[k] = std::min<unsigned long long>(B, (tg[k] + hash_cap - 1) / hash_cap);
+                at[k] = idx[k] * hash_cap;
+            }
+            return cudaSuccess;
+        }
+        cudaError_t e = cudaSuccess;
+        if (z->pq.bytes < n * 24) {
+            cudaFree(z->pq.p);
+            z->pq.p = nullptr;
+            z->pq.bytes = 0;
+            e = cudaMalloc(&z->pq.p, n * 24 + 256);
+            if (e != cudaSuccess) return e;
+            z->pq.bytes = n * 24 + 256;
+        }
+        auto *dq = P<unsigned long long>(z->pq);
+        e = cudaMemcpyAsync(dq, tg.data(), n * 8, cudaMemcpyHostToDevice, z->st);
+        if (e == cudaSuccess) e = boff_lower_bounds(P<unsigned long long>(z->boff), B, dq, (int)n, dq + n, z->st);
+        std::vector<unsigned long long> out(2 * n);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), dq + n, n * 16, cudaMemcpyDeviceToHost, z->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(z->st);
+        for (size_t k = 0; k < n; ++k) idx[k] = out[2 * k], at[k] = out[2 * k + 1];
+        return e;
+    };
+    auto boff_at = [&](unsigned long long b, unsigned long long &v) -> cudaError_t {
+        if (!row_mode) {
+            v = b * hash_cap;
+            return cudaSuccess;
+        }
+        cudaError_t e = cudaMemcpyAsync(&v, P<unsigned long long>(z->boff) + b, 8, cudaMemcpyDeviceToHost, z->st);
+        return e == cudaSuccess ? cudaStreamSynchronize(z->st) : e;
+    };
 
     // streamed-output capacity: 16 N_d (the merge raises the threshold to keep
     // the stream within it) plus room for u's entries on w_i, w_{i-1}
@@ -431,8 +459,8 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         const double budget = avail - sig_bytes - 2.0 * ovf_cap * 16.0;  // for the element regions
         // passes: the fewest contiguous bucket ranges of about equal regions that
         // fit the budget (cut where the running region total crosses j/npass)
-        const unsigned long long total_slots = z->h_boff[B];
-        std::vector<unsigned long long> cuts;
+        const unsigned long long total_slots = total_cap;
+        std::vector<unsigned long long> cuts, coff;  // pass boundaries (buckets) and their region offsets
         unsigned long long max_pass = 0;
         const int npass0 = std::max(1, (int)std::min(1e6, std::ceil((double)total_slots * sizeof(Slot) /
                                                                    std::max(budget, 1.0))));
@@ -442,18 +470,23 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                 set_error("not enough device memory for one merge bucket");
                 return SFCI_E_CAPACITY;
             }
+            std::vector<unsigned long long> tg, idx, at;
+            for (int j = 1; j < npass; ++j) tg.push_back((unsigned long long)((double)total_slots * j / npass));
+            SFCI_CUDA(lower_bounds(tg, idx, at));
             cuts.assign(1, 0ull);
+            coff.assign(1, 0ull);
             for (int j = 1; j < npass; ++j) {
-                const unsigned long long at = (unsigned long long)((double)total_slots * j / npass);
-                unsigned long long c = (unsigned long long)(std::lower_bound(z->h_boff.begin(), z->h_boff.begin() + B,
-                                                                             at) - z->h_boff.begin());
-                c = std::max(c, cuts.back() + 1);
+                unsigned long long c = std::max(idx[j - 1], cuts.back() + 1);
                 c = std::min(c, B - (unsigned long long)(npass - j));
+                unsigned long long o = at[j - 1];
+                if (c != idx[j - 1]) SFCI_CUDA(boff_at(c, o));
                 cuts.push_back(c);
+                coff.push_back(o);
             }
             cuts.push_back(B);
+            coff.push_back(total_slots);
             max_pass = 0;
-            for (int j = 0; j < npass; ++j) max_pass = std::max(max_pass, z->h_boff[cuts[j + 1]] - z->h_boff[cuts[j]]);
+            for (int j = 0; j < npass; ++j) max_pass = std::max(max_pass, coff[j + 1] - coff[j]);
             if ((double)max_pass * sizeof(Slot) <= budget) break;
         }
         const size_t need_elem = size_t(max_pass) * sizeof(Slot);
@@ -530,17 +563,23 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         z->n_split = 0;
         // passes as bucket ranges; a range whose overflow outgrew the list is
         // split in two and emitted again (its merge has not run yet)
-        std::vector<std::pair<unsigned, unsigned>> ranges;
-        for (int pass = npass - 1; pass >= 0; --pass) ranges.emplace_back((unsigned)cuts[pass], (unsigned)cuts[pass + 1]);
+        struct Range {
+            unsigned lo, hi;              // buckets
+            unsigned long long olo, ohi;  // their region offsets
+        };
+        std::vector<Range> ranges;
+        for (int pass = npass - 1; pass >= 0; --pass)
+            ranges.push_back(Range{(unsigned)cuts[pass], (unsigned)cuts[pass + 1], coff[pass], coff[pass + 1]});
         while (!ranges.empty()) {
-            const unsigned lo = ranges.back().first, hi = ranges.back().second;
+            const Range rg = ranges.back();
+            const unsigned lo = rg.lo, hi = rg.hi;
             ranges.pop_back();
             SFCI_CUDA(cudaMemsetAsync(z->ovf_n, 0, 8, z->st));
             BucketOut bo;
             bo.bk = bk;
             bo.count = P<unsigned>(z->bcount);
             bo.elem = P<Slot>(z->belem);
-            bo.base = z->h_boff[lo];
+            bo.base = rg.olo;
             bo.eps_elem = z->p.eps_element > 0.0 ? z->p.eps_element : 0.0;
             bo.ovf = P<Slot>(z->bovf);
             bo.ovf_n = z->ovf_n;
@@ -549,21 +588,16 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             bo.row_lo = 0, bo.row_hi = ~0ull;
             if (row_mode) {
                 // rows are bucketed in order: the rows before the first one with a
-                // bucket at or above lo, and from the first one with a bucket at or
-                // above hi on, hold no bucket of this pass
-                auto last_b = [&](size_t k) { return (z->h_nzmap[k] >> 32) + (unsigned)z->h_nzmap[k]; };
-                size_t a = 0, e = z->h_nzrow.size();
-                while (a < e) {
-                    const size_t m = (a + e) / 2;
-                    if (last_b(m) > lo) e = m; else a = m + 1;
-                }
-                bo.row_lo = a == 0 ? 0ull : z->h_nzrow[a - 1] + 1;
-                a = 0, e = z->h_nzrow.size();
-                while (a < e) {
-                    const size_t m = (a + e) / 2;
-                    if ((z->h_nzmap[m] >> 32) >= hi) e = m; else a = m + 1;
-                }
-                bo.row_hi = a == z->h_nzrow.size() ? d.ca - 1 : z->h_nzrow[a] - 1;
+                // bucket at or above lo, and from the first one with all its
+                // buckets at or above hi on, hold no bucket of this pass
+                if ((r = ensure(z->pq, 256, z->st, "plan queries"))) return r;
+                unsigned long long lim[2];
+                SFCI_CUDA(pass_rows(P<unsigned long long>(z->rowmap), d.ca, lo, hi, P<unsigned long long>(z->pq),
+                                    z->st));
+                SFCI_CUDA(cudaMemcpyAsync(lim, z->pq.p, 16, cudaMemcpyDeviceToHost, z->st));
+                SFCI_CUDA(cudaStreamSynchronize(z->st));
+                bo.row_lo = lim[0];
+                bo.row_hi = lim[1] > 0 ? lim[1] - 1 : 0ull;
             }
             bo.status = z->mstatus;
             SFCI_CUDA(cudaEventRecord(z->evp[0], z->st));
@@ -590,16 +624,22 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                     hs2 &= ~2;  // the list's truncation bit: this range is emitted again in pieces
                     SFCI_CUDA(cudaMemcpyAsync(z->mstatus, &hs2, 4, cudaMemcpyHostToDevice, z->st));
                     SFCI_CUDA(cudaMemsetAsync(P<unsigned>(z->bcount) + lo, 0, size_t(hi - lo) * 4, z->st));
+                    std::vector<unsigned long long> tg, idx, at;
+                    for (unsigned j = 1; j < k; ++j) tg.push_back(rg.olo + (rg.ohi - rg.olo) * j / k);
+                    SFCI_CUDA(lower_bounds(tg, idx, at));
                     std::vector<unsigned> cut{lo};
-                    const unsigned long long r0 = z->h_boff[lo], r1 = z->h_boff[hi];
+                    std::vector<unsigned long long> co{rg.olo};
                     for (unsigned j = 1; j < k; ++j) {
-                        unsigned m = cut.back() + 1;
-                        const unsigned long long want_at = r0 + (r1 - r0) * j / k;
-                        while (m + (k - j) < hi && z->h_boff[m] < want_at) ++m;
-                        cut.push_back(m);
+                        unsigned long long m = std::max<unsigned long long>(idx[j - 1], cut.back() + 1);
+                        m = std::min<unsigned long long>(m, hi - (k - j));
+                        unsigned long long o = at[j - 1];
+                        if (m != idx[j - 1]) SFCI_CUDA(boff_at(m, o));
+                        cut.push_back((unsigned)m);
+                        co.push_back(o);
                     }
                     cut.push_back(hi);
-                    for (unsigned j = k; j > 0; --j) ranges.emplace_back(cut[j - 1], cut[j]);
+                    co.push_back(rg.ohi);
+                    for (unsigned j = k; j > 0; --j) ranges.push_back(Range{cut[j - 1], cut[j], co[j - 1], co[j]});
                     z->n_split += (int)k - 1;
                     continue;
                 }

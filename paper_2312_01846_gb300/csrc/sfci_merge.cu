@@ -129,9 +129,10 @@ __device__ __forceinline__ double from_fixed(unsigned long long lo, unsigned lon
 
 // ------------------------------------------------------------- scan
 
-// exclusive scan of unsigned 32-bit counts into 64-bit offsets, m entries,
-// out[m] = total; three kernels (block sums, scan of sums, block scans)
-__global__ void scan_sums_kernel(const unsigned *in, long long m, unsigned long long *bsum) {
+// exclusive scan of unsigned 32- or 64-bit counts into 64-bit offsets, m
+// entries, out[m] = total; three kernels (block sums, scan of sums, block scans)
+template <typename T>
+__global__ void scan_sums_kernel(const T *in, long long m, unsigned long long *bsum) {
     __shared__ unsigned long long w[32];
     const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
     unsigned long long v = i < m ? in[i] : 0;
@@ -179,7 +180,8 @@ __global__ void scan_top_kernel(unsigned long long *bsum, long long nb) {
     }
 }
 
-__global__ void scan_block_kernel(const unsigned *in, long long m, const unsigned long long *bsum,
+template <typename T>
+__global__ void scan_block_kernel(const T *in, long long m, const unsigned long long *bsum,
                                   unsigned long long *out) {
     __shared__ unsigned long long w[32];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -679,8 +681,9 @@ size_t scan_ws_bytes(long long m) {
     return size_t(nb > 0 ? nb : 1) * 8;
 }
 
-cudaError_t exclusive_scan(const unsigned *in, long long m, unsigned long long *out, void *ws,
-                           cudaStream_t st) {
+namespace {
+template <typename T>
+cudaError_t exclusive_scan_t(const T *in, long long m, unsigned long long *out, void *ws, cudaStream_t st) {
     if (m <= 0) return cudaMemsetAsync(out, 0, 8, st);
     const long long nb = (m + 1023) / 1024;
     unsigned long long *bsum = static_cast<unsigned long long *>(ws);
@@ -691,6 +694,17 @@ cudaError_t exclusive_scan(const unsigned *in, long long m, unsigned long long *
     count_launch();
     scan_block_kernel<<<(unsigned)nb, 1024, 0, st>>>(in, m, bsum, out);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t exclusive_scan(const unsigned *in, long long m, unsigned long long *out, void *ws,
+                           cudaStream_t st) {
+    return exclusive_scan_t(in, m, out, ws, st);
+}
+
+cudaError_t exclusive_scan(const unsigned long long *in, long long m, unsigned long long *out, void *ws,
+                           cudaStream_t st) {
+    return exclusive_scan_t(in, m, out, ws, st);
 }
 
 cudaError_t sort_overflow(const Buckets &bk, const unsigned *count, unsigned lo, unsigned nb,
