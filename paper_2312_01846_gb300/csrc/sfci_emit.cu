@@ -645,7 +645,8 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
 // weights[ha] += elements bound for row ha: the source's own row gets the
 // diagonal, its beta singles and beta-beta doubles; each alpha single's row
 // gets the single plus one element per beta hop; each alpha-alpha double's row
-// gets one element.  One warp per input determinant.
+// gets one element.  One warp per input determinant (per run of determinants
+// sharing alpha when nothing is screened).
 __global__ void __launch_bounds__(kEmitThreads)
 row_weight_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                   const double *__restrict__ in_coef, long long n_in, double eps,
@@ -672,6 +673,24 @@ row_weight_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank
     for (long long s = gw; s < n_in; s += nw) {
         const unsigned long long r = in_rank[s];
         const unsigned long long hA = r / cb;
+        unsigned long long mult = 1;
+        if (!(eps > 0.0)) {
+            // without the screen the weights depend on alpha only: the first
+            // source of each run of consecutive sources sharing alpha (the
+            // input is sorted by rank, alpha-major) adds them times the run length
+            if (s > 0 && in_rank[s - 1] / cb == hA) continue;
+            long long e = s + 1;
+            for (;;) {
+                const long long q = e + lane;
+                const unsigned bal = __ballot_sync(kFull, q < n_in && in_rank[q] / cb == hA);
+                if (bal != kFull) {
+                    e += __ffs(~bal) - 1;
+                    break;
+                }
+                e += 32;
+            }
+            mult = (unsigned long long)(e - s);
+        }
         const unsigned long long alpha = string_unrank_warp(hA, n, d.na, bt, ks);
         const double ac = eps > 0.0 ? fabs(in_coef[s]) : 0.0;
         unsigned long long beta = 0;
@@ -686,13 +705,13 @@ row_weight_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank
                     if (!(ac * __ldg(&d.bound_ss[occB[pOB[2 * p]] * n + occB[pOB[2 * p + 1]]]) < eps))
                         w += (unsigned long long)d.pv_b;
             }
-            atomicAdd(&weights[hA], w);
+            atomicAdd(&weights[hA], w * mult);
         }
         for (int x = lane; x < d.sa; x += 32) {
             const int io = x / d.va, iv = x - io * d.va;
             const bool hops = !(eps > 0.0 && ac * __ldg(&d.bound_ab[virA[iv] * n + occA[io]]) < eps);
             atomicAdd(&weights[string_rank(alpha ^ (1ull << occA[io]) ^ (1ull << virA[iv]), bt, ks)],
-                      hops ? w_single : 1ull);
+                      (hops ? w_single : 1ull) * mult);
         }
         for (int p = 0; p < d.po_a; ++p) {
             const int io = pOA[2 * p], jo = pOA[2 * p + 1];
@@ -700,7 +719,7 @@ row_weight_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank
             const unsigned long long rem = alpha ^ (1ull << occA[io]) ^ (1ull << occA[jo]);
             pair_prefix(occA, d.na, io, jo, bt, ks, pre);
             for (int q = lane; q < d.pv_a; q += 32)
-                atomicAdd(&weights[pair_rank(rem, virA[pVA[2 * q]], virA[pVA[2 * q + 1]], d.na, pre, bt, ks)], 1ull);
+                atomicAdd(&weights[pair_rank(rem, virA[pVA[2 * q]], virA[pVA[2 * q + 1]], d.na, pre, bt, ks)], mult);
             __syncwarp();
         }
     }
