@@ -37,6 +37,10 @@ if ROOT not in sys.path:
 METRIC = "σ=Hψ connected elements/s & Lanczos steps/s vs plain FP64 at ΔE≤1 µHa"
 UNIT = "connected elements/s"
 BYTES_PER_ELEMENT = 32  # 16 B intermediate element written + 16 B read back by the merge
+# DRAM bytes per connected element that ncu measured for emit_kernel + merge_kernel
+# together (dram__bytes_read.sum + dram__bytes_write.sum of one launch each on the same
+# workload at N_d = 5e3, 1.5362e8 elements, one pass); scaled by the elements of a step
+MEASURED_DRAM_BYTES_PER_ELEMENT = (0.131032 + 2.492552 + 2.481910 + 0.004696) * 1e9 / 1.5362e8
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -439,7 +443,9 @@ def run_ours(a):
     hbm, peak_kind = peaks()
     achieved = BYTES_PER_ELEMENT * el_per_launch / (ms_sig * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
+                "frac": achieved / hbm, "traffic": MEASURED_DRAM_BYTES_PER_ELEMENT * el_per_launch,
+                "traffic_note": "bytes per launch: ncu DRAM bytes per element of emit_kernel + "
+                                "merge_kernel (N_d = 5e3 capture, one pass) x elements per launch",
                 "kernel": "sigma stage: emit_kernel + merge_kernel",
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "model": f"{BYTES_PER_ELEMENT} B per connected element (16 B written by emit, "
