@@ -178,31 +178,23 @@ __device__ __forceinline__ void overflow_append(const BucketOut &B, bool of, con
 __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, const unsigned *bk,
                                             const unsigned long long *tg, const double *v,
                                             unsigned long long *cur) {
-    // lanes reserve by runs of consecutive lanes bound for one bucket (the
-    // elements of one target row sit in consecutive lanes): the first lane of
-    // a run takes the run's places with one atomic
-    const unsigned lane = threadIdx.x & 31;
-    const unsigned le = 0xffffffffu >> (31 - lane);  // lanes 0..lane
-    unsigned lead[kU], base[kU];
+    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    unsigned peers[kU], base[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) peers[k] = __match_any_sync(kFull, ok[k] ? bk[k] : (0x80000000u | lane));
 #pragma unroll
     for (int k = 0; k < kU; ++k) {
-        const unsigned key = ok[k] ? bk[k] : (0x80000000u | lane);
-        const unsigned prev = __shfl_up_sync(kFull, key, 1);
-        const unsigned starts = __ballot_sync(kFull, lane == 0 || prev != key);
-        lead[k] = 31 - __clz(starts & le);
-        const unsigned above = starts & ~le;
-        const unsigned next = above ? (unsigned)__ffs(above) - 1 : 32u;
         base[k] = 0;
-        if (ok[k] && lead[k] == lane) base[k] = atomicAdd(&B.count[bk[k]], next - lane);
+        if (ok[k] && (peers[k] & lt) == 0) base[k] = atomicAdd(&B.count[bk[k]], (unsigned)__popc(peers[k]));
     }
 #pragma unroll
-    for (int k = 0; k < kU; ++k) base[k] = __shfl_sync(kFull, base[k], lead[k]);
+    for (int k = 0; k < kU; ++k) base[k] = __shfl_sync(kFull, base[k], __ffs(peers[k]) - 1);
 #pragma unroll
     for (int k = 0; k < kU; ++k) {
         bool of = false;
         const ulonglong2 sl = make_ulonglong2(tg[k], (unsigned long long)__double_as_longlong(v[k]));
         if (ok[k]) {
-            const unsigned pos = base[k] + (lane - lead[k]);
+            const unsigned pos = base[k] + __popc(peers[k] & lt);
             const unsigned long long o0 = __ldg(&B.bk.boff[bk[k]]), o1 = __ldg(&B.bk.boff[bk[k] + 1]);
             if (pos < o1 - o0) reinterpret_cast<ulonglong2 *>(B.elem)[o0 - B.base + pos] = sl;
             else of = true;
