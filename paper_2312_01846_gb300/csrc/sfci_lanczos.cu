@@ -453,8 +453,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         // memory the element regions may use: what is free plus what the big buffers hold
         const double held = (double)z->belem.bytes + (double)z->sig_key.bytes + (double)z->sig_val.bytes +
                             (double)z->bovf.bytes + (double)z->bovf_sorted.bytes;
-        // (less 4 % and 6 GB for the per-bucket arrays, probes and the truncation's buffers)
-        double avail = 0.96 * ((double)free_b + held) - 6e9;
+        double avail = 0.85 * ((double)free_b + held);
         if (z->p.mem_budget > 0) avail = std::min(avail, (double)z->p.mem_budget);
         const double sig_bytes = 1.1 * sig_need * 16.0;
         const double budget = avail - sig_bytes - 2.0 * ovf_cap * 16.0;  // for the element regions

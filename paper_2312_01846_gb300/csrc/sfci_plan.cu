@@ -41,7 +41,7 @@ __global__ void plan_count_kernel(const unsigned *tl, const unsigned *th, unsign
 
 // row map entry (first bucket << 32 | bucket count) and bucket capacities:
 // light buckets hold exactly their rows' counts; a heavy row's buckets get
-// the mean plus two standard deviations plus 16 of its beta-hash split (the
+// the mean plus four standard deviations plus 32 of its beta-hash split (the
 // rest spills to the overflow list), a one-bucket heavy row exactly its count
 // (rows must arrive in window order: P even, windows of P/2)
 __global__ void plan_rows_kernel(const unsigned long long *w, const unsigned long long *wpre,
@@ -65,7 +65,7 @@ __global__ void plan_rows_kernel(const unsigned long long *w, const unsigned lon
                 per = (unsigned)wr;
             } else {
                 const double mu = (double)wr / (double)ns;
-                per = (unsigned)ceil(mu + 2.0 * sqrt(mu) + 16.0);
+                per = (unsigned)ceil(mu + 4.0 * sqrt(mu) + 32.0);
             }
             for (unsigned long long j = 0; j < ns; ++j) cap[first + j] = per;
         } else {
