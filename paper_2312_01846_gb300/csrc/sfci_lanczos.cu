@@ -346,7 +346,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         SFCI_CUDA(exclusive_scan(static_cast<const unsigned long long *>(w), (long long)nrows,
                                  P<unsigned long long>(z->wpre), z->scan_ws.p, z->st));
         // windows: light flag in ptl, heavy bucket count in pth, their sum back in pth
-        SFCI_CUDA(plan_windows(w, P<unsigned long long>(z->wpre), nrows, Pb, T, P<unsigned>(z->ptl),
+        SFCI_CUDA(plan_windows(w, P<unsigned long long>(z->wpre), nrows, Pb, d.cb, T, P<unsigned>(z->ptl),
                                P<unsigned>(z->pth), P<unsigned>(z->pth), z->st));
         SFCI_CUDA(exclusive_scan(static_cast<const unsigned *>(P<unsigned>(z->pth)), (long long)T,
                                  P<unsigned long long>(z->pbstart), z->scan_ws.p, z->st));
@@ -361,7 +361,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if ((r = ensure(z->scan_ws, scan_ws_bytes((long long)std::max({T, nrows, B}) + 1), z->st, "scan workspace",
                         1.5)))
             return r;
-        SFCI_CUDA(plan_rows(w, P<unsigned long long>(z->wpre), nrows, Pb, P<unsigned>(z->ptl),
+        SFCI_CUDA(plan_rows(w, P<unsigned long long>(z->wpre), nrows, Pb, d.cb, P<unsigned>(z->ptl),
                             P<unsigned long long>(z->pbstart), B, P<unsigned long long>(z->rowmap),
                             P<unsigned>(z->pcap), z->st));
         SFCI_CUDA(exclusive_scan(static_cast<const unsigned *>(P<unsigned>(z->pcap)), (long long)B,

@@ -7,10 +7,15 @@
 //   - a light row (0 < w <= Q) joins the light bucket of the window
 //     floor(W(r) / Q) it starts in; the rows of one light bucket are
 //     consecutive and hold at most Q + Q = P elements;
-//   - a heavy row (w > Q) gets ns = ceil(w / P) buckets of its own, after the
-//     light bucket of the window it starts in.  It spans more than a window,
-//     so the next row starts in a later one: a window holds light rows, then
-//     at most one heavy row.
+//   - a heavy row (w > Q) gets ns = min(ceil(w / P), ceil(C / P)) buckets of
+//     its own (C: beta strings), after the light bucket of the window it
+//     starts in.  It spans more than a window, so the next row starts in a
+//     later one: a window holds light rows, then at most one heavy row.
+//     The split is by a hash of the beta index, so a bucket of a row with
+//     ns = ceil(C / P) can hold no more distinct keys than the beta strings
+//     hashed to it (about P): the rows that many sources reach (w > C, their
+//     keys repeated many times) get fewer, larger buckets, which the merge
+//     table still holds and whose regions overflow far less.
 // Buckets are numbered window by window, so alpha rows and buckets are in the
 // same order and every light bucket is a contiguous rank range.
 #include <cstdint>
@@ -20,15 +25,21 @@
 namespace sfci {
 namespace {
 
+__device__ __forceinline__ unsigned long long heavy_buckets(unsigned long long wr, unsigned long long P,
+                                                         unsigned long long C) {
+    const unsigned long long by_w = (wr + P - 1) / P, by_keys = (C + P - 1) / P;
+    return by_w < by_keys ? by_w : by_keys;
+}
+
 __global__ void plan_windows_kernel(const unsigned long long *w, const unsigned long long *wpre,
-                                    unsigned long long nrows, unsigned long long P, unsigned *tl,
-                                    unsigned *th) {
+                                    unsigned long long nrows, unsigned long long P, unsigned long long C,
+                                    unsigned *tl, unsigned *th) {
     for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nrows;
          r += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long wr = w[r];
         if (!wr) continue;
         const unsigned long long t = wpre[r] / (P / 2);
-        if (wr > P / 2) th[t] = (unsigned)((wr + P - 1) / P);
+        if (wr > P / 2) th[t] = (unsigned)heavy_buckets(wr, P, C);
         else tl[t] = 1u;
     }
 }
@@ -45,8 +56,8 @@ __global__ void plan_count_kernel(const unsigned *tl, const unsigned *th, unsign
 // rest spills to the overflow list), a one-bucket heavy row exactly its count
 // (rows must arrive in window order: P even, windows of P/2)
 __global__ void plan_rows_kernel(const unsigned long long *w, const unsigned long long *wpre,
-                                 unsigned long long nrows, unsigned long long P, const unsigned *tl,
-                                 const unsigned long long *bstart,
+                                 unsigned long long nrows, unsigned long long P, unsigned long long C,
+                                 const unsigned *tl, const unsigned long long *bstart,
                                  unsigned long long *rowmap, unsigned *cap) {
     for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nrows;
          r += (unsigned long long)gridDim.x * blockDim.x) {
@@ -57,7 +68,7 @@ __global__ void plan_rows_kernel(const unsigned long long *w, const unsigned lon
         }
         const unsigned long long t = wpre[r] / (P / 2);
         if (wr > P / 2) {
-            const unsigned long long ns = (wr + P - 1) / P;
+            const unsigned long long ns = heavy_buckets(wr, P, C);
             const unsigned long long first = bstart[t] + tl[t];
             rowmap[r] = (first << 32) | ns;
             unsigned per;
@@ -115,26 +126,26 @@ unsigned grid_of(unsigned long long n) {
 }  // namespace
 
 cudaError_t plan_windows(const unsigned long long *w, const unsigned long long *wpre, unsigned long long nrows,
-                         unsigned long long P, unsigned long long T, unsigned *tl, unsigned *th, unsigned *tc,
-                         cudaStream_t st) {
+                         unsigned long long P, unsigned long long C, unsigned long long T, unsigned *tl, unsigned *th,
+                         unsigned *tc, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(tl, 0, size_t(T) * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(th, 0, size_t(T) * 4, st);
     if (e != cudaSuccess) return e;
     count_launch();
-    plan_windows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, wpre, nrows, P, tl, th);
+    plan_windows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, wpre, nrows, P, C, tl, th);
     count_launch();
     plan_count_kernel<<<grid_of(T), 256, 0, st>>>(tl, th, T, tc);
     return cudaGetLastError();
 }
 
 cudaError_t plan_rows(const unsigned long long *w, const unsigned long long *wpre, unsigned long long nrows,
-                      unsigned long long P, const unsigned *tl,
+                      unsigned long long P, unsigned long long C, const unsigned *tl,
                       const unsigned long long *bstart, unsigned long long B, unsigned long long *rowmap,
                       unsigned *cap, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(cap, 0, size_t(B) * 4, st);
     if (e != cudaSuccess) return e;
     count_launch();
-    plan_rows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, wpre, nrows, P, tl, bstart, rowmap, cap);
+    plan_rows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, wpre, nrows, P, C, tl, bstart, rowmap, cap);
     return cudaGetLastError();
 }
 
