@@ -195,8 +195,9 @@ __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, 
         const ulonglong2 sl = make_ulonglong2(tg[k], (unsigned long long)__double_as_longlong(v[k]));
         if (ok[k]) {
             const unsigned pos = base[k] + __popc(peers[k] & lt);
-            const unsigned long long o0 = __ldg(&B.bk.boff[bk[k]]), o1 = __ldg(&B.bk.boff[bk[k] + 1]);
-            if (pos < o1 - o0) reinterpret_cast<ulonglong2 *>(B.elem)[o0 - B.base + pos] = sl;
+            const unsigned long long o0 = (unsigned long long)__ldg(&B.start4[bk[k]]) << 2;
+            const unsigned long long o1 = (unsigned long long)__ldg(&B.start4[bk[k] + 1]) << 2;
+            if (pos < o1 - o0) reinterpret_cast<ulonglong2 *>(B.elem)[o0 + pos] = sl;
             else of = true;
         }
         overflow_append(B, of, sl, cur);
@@ -276,8 +277,9 @@ __device__ __forceinline__ void single_append(const BucketOut &B, unsigned b, co
     unsigned base = 0;
     if (lane == 0) base = atomicAdd(&B.count[b], tot);
     base = __shfl_sync(kFull, base, 0);
-    const unsigned long long o0 = __ldg(&B.bk.boff[b]), cap = __ldg(&B.bk.boff[b + 1]) - o0;
-    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(B.elem) + (o0 - B.base);
+    const unsigned long long o0 = (unsigned long long)__ldg(&B.start4[b]) << 2;
+    const unsigned long long cap = ((unsigned long long)__ldg(&B.start4[b + 1]) << 2) - o0;
+    ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(B.elem) + o0;
 #pragma unroll
     for (int k = 0; k < kU; ++k) {
         bool of = false;

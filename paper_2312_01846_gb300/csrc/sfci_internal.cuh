@@ -244,6 +244,8 @@ struct BucketOut {
     unsigned *count;          // [B] elements that arrived per bucket
     Slot *elem;               // regions of buckets [lo, hi), relative to boff[lo]
     unsigned long long base;  // boff[lo]
+    const unsigned *start4;   // [B + 1]: (boff[b] - boff[lo]) / 4 for b in [lo, hi] (regions are
+                              // multiples of 4 slots): the pass's offsets in half the bytes
     double eps_elem;          // elements with |<D'|H|D> c_D| < eps_elem are not generated (0: off)
     Slot *ovf;                // [ovf_cap]
     unsigned long long *ovf_n;
@@ -406,6 +408,11 @@ cudaError_t plan_rows(const unsigned long long *w, const unsigned long long *wpr
 // out[2k] = first bucket b <= nb with boff[b] >= targets[k], out[2k+1] = boff[b]
 cudaError_t boff_lower_bounds(const unsigned long long *boff, unsigned long long nb,
                               const unsigned long long *targets, int n, unsigned long long *out, cudaStream_t st);
+// start4[b] = (boff[b] - boff[lo]) / 4 for b in [lo, hi]
+cudaError_t pass_offsets(const unsigned long long *boff, unsigned lo, unsigned hi, unsigned *start4,
+                         cudaStream_t st);
+// cap[b] rounded up to a multiple of 4
+cudaError_t round_caps4(unsigned *cap, unsigned long long nb, cudaStream_t st);
 // lim[0] = first alpha row that can hold buckets [lo, hi), lim[1] = one past the last
 cudaError_t pass_rows(const unsigned long long *rowmap, unsigned long long nrows, unsigned lo, unsigned hi,
                       unsigned long long *lim, cudaStream_t st);

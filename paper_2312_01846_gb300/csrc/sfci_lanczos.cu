@@ -179,7 +179,8 @@ struct sfci_lanczos {
     };
     Buf bcount, belem, bovf, bovf_sorted, tmp_counts, ovf_off, probes, pcount, poff, scan_ws,
         sig_key, sig_val, cand_key, cand_val, weights, rowmap, boff,
-        wpre, ptl, pth, pbstart, pcap, pq;  // device bucket plan (row mode)
+        wpre, ptl, pth, pbstart, pcap, pq,  // device bucket plan (row mode)
+        start4;                             // region offsets of the current pass
     long long sig_cap = 0, ovf_cap = 0, cand_cap = 0;
     double *sigw[kMaxVec] = {};
     char *words = nullptr;  // hist[kHistBins] | outn | mlive | ovf_n | cand_n | msumsq | queue | mstatus | nnz | dmin | tau | mark | lock
@@ -213,7 +214,7 @@ void destroy_lz(sfci_lanczos *z) {
     for (auto *b : {&z->bcount, &z->belem, &z->bovf, &z->bovf_sorted, &z->tmp_counts, &z->ovf_off,
                     &z->probes, &z->pcount, &z->poff, &z->scan_ws, &z->sig_key, &z->sig_val,
                     &z->cand_key, &z->cand_val, &z->weights, &z->rowmap, &z->boff, &z->wpre, &z->ptl,
-                    &z->pth, &z->pbstart, &z->pcap, &z->pq})
+                    &z->pth, &z->pbstart, &z->pcap, &z->pq, &z->start4})
         cudaFree(b->p);
     cudaFree(z->words);
     for (int j = 0; j < kMaxVec; ++j) cudaFree(z->sigw[j]);
@@ -364,6 +365,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         SFCI_CUDA(plan_rows(w, P<unsigned long long>(z->wpre), nrows, Pb, d.cb, P<unsigned>(z->ptl),
                             P<unsigned long long>(z->pbstart), B, P<unsigned long long>(z->rowmap),
                             P<unsigned>(z->pcap), z->st));
+        SFCI_CUDA(round_caps4(P<unsigned>(z->pcap), B, z->st));
         SFCI_CUDA(exclusive_scan(static_cast<const unsigned *>(P<unsigned>(z->pcap)), (long long)B,
                                  P<unsigned long long>(z->boff), z->scan_ws.p, z->st));
         SFCI_CUDA(cudaMemcpyAsync(&total_cap, P<unsigned long long>(z->boff) + B, 8, cudaMemcpyDeviceToHost, z->st));
@@ -456,7 +458,8 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         double avail = 0.85 * ((double)free_b + held);
         if (z->p.mem_budget > 0) avail = std::min(avail, (double)z->p.mem_budget);
         const double sig_bytes = 1.1 * sig_need * 16.0;
-        const double budget = avail - sig_bytes - 2.0 * ovf_cap * 16.0;  // for the element regions
+        // for the element regions (a pass's region offsets are 32-bit counts of 4 slots)
+        const double budget = std::min(avail - sig_bytes - 2.0 * ovf_cap * 16.0, 4.0 * 4294967295.0 * sizeof(Slot));
         // passes: the fewest contiguous bucket ranges of about equal regions that
         // fit the budget (cut where the running region total crosses j/npass)
         const unsigned long long total_slots = total_cap;
@@ -521,6 +524,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         ovf_cap = std::min((long long)(std::min(z->bovf.bytes, z->bovf_sorted.bytes) / sizeof(Slot)), ovf_lim);
         z->ovf_cap = ovf_cap;
         if ((r = ensure(z->bcount, size_t(B) * 4, z->st, "bucket counters", 1.5))) return r;
+        if ((r = ensure(z->start4, size_t(B + 1) * 4, z->st, "pass offsets", 1.5))) return r;
         if ((r = ensure(z->probes, size_t(std::max<long long>(totp, 1)) * sizeof(Probe), z->st, "probes"))) return r;
         if ((r = ensure(z->pcount, size_t(B) * 4, z->st, "probe counts", 1.5))) return r;
         if ((r = ensure(z->poff, size_t(B + 1) * 8, z->st, "probe offsets", 1.5))) return r;
@@ -580,6 +584,8 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             bo.count = P<unsigned>(z->bcount);
             bo.elem = P<Slot>(z->belem);
             bo.base = rg.olo;
+            SFCI_CUDA(pass_offsets(P<unsigned long long>(z->boff), lo, hi, P<unsigned>(z->start4), z->st));
+            bo.start4 = P<unsigned>(z->start4);
             bo.eps_elem = z->p.eps_element > 0.0 ? z->p.eps_element : 0.0;
             bo.ovf = P<Slot>(z->bovf);
             bo.ovf_n = z->ovf_n;

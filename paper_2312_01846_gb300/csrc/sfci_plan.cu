@@ -118,6 +118,19 @@ __global__ void pass_rows_kernel(const unsigned long long *rowmap, unsigned long
     }
 }
 
+__global__ void pass_offsets_kernel(const unsigned long long *boff, unsigned lo, unsigned hi, unsigned *start4) {
+    const unsigned long long base = boff[lo];
+    for (unsigned long long b = lo + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; b <= hi;
+         b += (unsigned long long)gridDim.x * blockDim.x)
+        start4[b] = (unsigned)((boff[b] - base) >> 2);
+}
+
+__global__ void round_caps4_kernel(unsigned *cap, unsigned long long nb) {
+    for (unsigned long long b = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; b < nb;
+         b += (unsigned long long)gridDim.x * blockDim.x)
+        cap[b] = (cap[b] + 3u) & ~3u;
+}
+
 unsigned grid_of(unsigned long long n) {
     const unsigned long long g = (n + 255) / 256;
     return (unsigned)(g < 16384 ? (g > 0 ? g : 1) : 16384);
@@ -164,6 +177,20 @@ cudaError_t pass_rows(const unsigned long long *rowmap, unsigned long long nrows
     if (e != cudaSuccess) return e;
     count_launch();
     pass_rows_kernel<<<grid_of(nrows), 256, 0, st>>>(rowmap, nrows, lo, hi, lim);
+    return cudaGetLastError();
+}
+
+cudaError_t pass_offsets(const unsigned long long *boff, unsigned lo, unsigned hi, unsigned *start4,
+                         cudaStream_t st) {
+    count_launch();
+    pass_offsets_kernel<<<grid_of((unsigned long long)(hi - lo) + 1), 256, 0, st>>>(boff, lo, hi, start4);
+    return cudaGetLastError();
+}
+
+cudaError_t round_caps4(unsigned *cap, unsigned long long nb, cudaStream_t st) {
+    if (!nb) return cudaSuccess;
+    count_launch();
+    round_caps4_kernel<<<grid_of(nb), 256, 0, st>>>(cap, nb);
     return cudaGetLastError();
 }
 
