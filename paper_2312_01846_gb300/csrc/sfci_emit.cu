@@ -197,7 +197,7 @@ __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, 
             const unsigned pos = base[k] + __popc(peers[k] & lt);
             const unsigned long long o0 = (unsigned long long)__ldg(&B.start4[bk[k]]) << 2;
             const unsigned long long o1 = (unsigned long long)__ldg(&B.start4[bk[k] + 1]) << 2;
-            if (pos < o1 - o0) reinterpret_cast<ulonglong2 *>(B.elem)[o0 + pos] = sl;
+            if (pos < o1 - o0) __stcs(reinterpret_cast<ulonglong2 *>(B.elem) + o0 + pos, sl);  // streamed: read once by the merge
             else of = true;
         }
         overflow_append(B, of, sl, cur);
@@ -286,7 +286,7 @@ __device__ __forceinline__ void single_append(const BucketOut &B, unsigned b, co
         const ulonglong2 sl = make_ulonglong2(tg[k], (unsigned long long)__double_as_longlong(v[k]));
         if (ok[k]) {
             const unsigned pos = base + pre[k];
-            if (pos < cap) dst[pos] = sl;
+            if (pos < cap) __stcs(dst + pos, sl);
             else of = true;
         }
         overflow_append(B, of, sl, cur);
