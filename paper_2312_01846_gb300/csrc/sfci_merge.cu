@@ -394,7 +394,7 @@ merge_kernel(MergeArgs A) {
             for (int k = 0; k < kPre; ++k) {
                 const unsigned e = e0 + k * kMT + tid;
                 x[k] = make_ulonglong2(kEmpty, 0ull);
-                if (e < total) x[k] = e < n_main ? src[e] : ovs[e - n_main];
+                if (e < total) x[k] = e < n_main ? __ldcs(src + e) : __ldcs(ovs + (e - n_main));  // read once
             }
             const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
