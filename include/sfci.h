@@ -111,7 +111,8 @@ sfci_status sfci_unrank(const sfci_system *sys, const uint64_t *rank, uint64_t *
 
 /* Workspace (bytes, device) that sfci_sigma needs for n_in input entries and
  * room for out_cap output entries.  It holds an open-addressing table of
- * 2^ceil(log2(2 out_cap)) slots (at least 1024) plus sort buffers. */
+ * 2^ceil(log2(2 out_cap)) slots (at least 1024; 32 bytes each with the exact
+ * sums) plus sort buffers. */
 sfci_status sfci_sigma_workspace_bytes(const sfci_system *sys, int64_t n_in, int64_t out_cap,
                                        size_t *bytes);
 
@@ -128,8 +129,11 @@ sfci_status sfci_sigma_workspace_bytes(const sfci_system *sys, int64_t n_in, int
  * the exact count when it is at most the table's slot count, otherwise a lower
  * bound (retry with a larger out_cap).  SFCI_E_CAPACITY also when ws_bytes is
  * below sfci_sigma_workspace_bytes.  No allocation; synchronises the stream.
- * Summation order inside an entry is not fixed (atomic adds), so results agree
- * with an ordered sum to rounding. */
+ * Each entry is summed exactly (128-bit fixed point in units of 2^-S, S set
+ * from (n_conn + 1) max|h, g element| max|c_D| so that no sum leaves the
+ * range) and rounded once to float64: the result does not depend on the order
+ * of the adds and is the same on every run.  SFCI_E_INVALID for non-finite
+ * coefficients. */
 sfci_status sfci_sigma(const sfci_system *sys, const uint64_t *in_rank, const double *in_coef,
                        int64_t n_in, double eps_screen, uint64_t *out_rank, double *out_coef,
                        int64_t out_cap, int64_t *n_out, void *workspace, size_t ws_bytes,

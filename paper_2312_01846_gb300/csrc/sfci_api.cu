@@ -51,7 +51,7 @@ int key_bits(unsigned long long dim) {
 // Layout of sfci_sigma's workspace.
 struct SigmaLayout {
     unsigned long long slots;
-    size_t table, status, count, ndev, flag, screened, sortws, bytes;
+    size_t table, acc, status, count, ndev, flag, screened, maxabs, sortws, bytes;
 };
 
 SigmaLayout sigma_layout(long long out_cap) {
@@ -60,11 +60,13 @@ SigmaLayout sigma_layout(long long out_cap) {
     L.slots = next_pow2(want < 1024 ? 1024 : want);
     size_t o = 0;
     L.table = o, o = a256(o + L.slots * sizeof(Slot));
+    L.acc = o, o = a256(o + L.slots * 16);  // exact sums, 128 bits per slot
     L.status = o, o = a256(o + sizeof(int));
     L.count = o, o = a256(o + sizeof(unsigned long long));
     L.ndev = o, o = a256(o + sizeof(unsigned long long));
     L.flag = o, o = a256(o + sizeof(int));
     L.screened = o, o = a256(o + sizeof(unsigned long long));
+    L.maxabs = o, o = a256(o + sizeof(unsigned long long));
     L.sortws = o, o = a256(o + sort_pairs_bytes(out_cap > 0 ? out_cap : 1));
     L.bytes = o;
     return L;
@@ -357,8 +359,21 @@ sfci_status sfci_sigma(const sfci_system *s, const uint64_t *in_rank, const doub
     const unsigned long long *ir = reinterpret_cast<const unsigned long long *>(in_rank);
     SFCI_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
     SFCI_CUDA(validate_sorted(ir, n_in, s->d.dim, flag, st));
+    // exact sums: units 2^-S with no entry beyond (n_conn + 1) hbound max|c| < 2^125 units
+    unsigned long long mbits = 0;
+    SFCI_CUDA(max_abs_bits(in_coef, n_in, reinterpret_cast<unsigned long long *>(w + L.maxabs), st));
+    SFCI_CUDA(cudaMemcpyAsync(&mbits, w + L.maxabs, 8, cudaMemcpyDeviceToHost, st));
+    SFCI_CUDA(cudaStreamSynchronize(st));
+    double cmax = 0.0;
+    std::memcpy(&cmax, &mbits, 8);
+    if (!std::isfinite(cmax)) return invalid("non-finite input coefficients");
+    t.acc = reinterpret_cast<unsigned long long *>(w + L.acc);
+    t.fix_shift = (int)std::floor(125.0 - std::log2(std::max(1e-300, (double)(s->d.n_conn + 1) * s->d.hbound *
+                                                                         std::max(cmax, 1e-300))));
+    t.fix_shift = std::max(-900, std::min(1000, t.fix_shift));
     SFCI_CUDA(table_clear(t, st));
     SFCI_CUDA(launch_emit(s->d, ir, in_coef, n_in, t, st));
+    SFCI_CUDA(table_finalize_exact(t, st));
     SFCI_CUDA(table_extract(t, eps_screen > 0.0 ? eps_screen : 0.0,
                             reinterpret_cast<unsigned long long *>(out_rank), out_coef, out_cap,
                             ndev, st));
@@ -374,6 +389,10 @@ sfci_status sfci_sigma(const sfci_system *s, const uint64_t *in_rank, const doub
     if (hflag) {
         *n_out = 0;
         return invalid("input ranks must be strictly ascending and below dim");
+    }
+    if (hstatus & 2) {
+        *n_out = 0;
+        return invalid("an element fell outside the fixed-point range of the exact sums");
     }
     if (hstatus & 1) {
         *n_out = (int64_t)(hcount + 1);

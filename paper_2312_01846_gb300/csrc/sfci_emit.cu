@@ -330,7 +330,9 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
         for (int k = 0; k < kU; ++k) {
             if (!want[k]) continue;
             const double v = __dmul_rn(e[k], c);
-            if (nonzero(v)) table_add(o.t, ha[k] * cb + hb[k], v, inserted);
+            if (!nonzero(v)) continue;
+            if (o.t.acc) table_add_exact(o.t, ha[k] * cb + hb[k], v, inserted);
+            else table_add(o.t, ha[k] * cb + hb[k], v, inserted);
         }
     } else {
         if (single == -2) return;

@@ -28,13 +28,91 @@ struct Slot {
     double val;
 };
 
+// Exact sums (used by the bucket merge and by sfci_sigma's table).
+// Each sigma entry is accumulated as a 128-bit two's-complement integer in
+// units of 2^-S (S chosen by the host so that no sum leaves the range): an
+// element v = m 2^e (m < 2^53) becomes m 2^(e+S), exactly unless e + S < 0
+// (|v| below 2^(52-S), rounded to the nearest unit).  Integer atomics add
+// them, so the sum is exact and independent of the order of the adds, and one
+// correctly rounded conversion gives the entry's double.
+
+struct Fix128 {
+    unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ Fix128 to_fixed(double v, int S, bool &range_ok) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
+    int ex = (int)((bits >> 52) & 0x7FF);
+    Fix128 x{0ull, 0ull};
+    if (ex == 0 && mant == 0) return x;
+    if (ex) mant |= 1ull << 52;
+    else ex = 1;
+    const int sh = ex - 1075 + S;  // v = mant 2^(ex-1075)
+    if (sh > 74) {                 // would not fit in 127 bits
+        range_ok = false;
+        return x;
+    }
+    if (sh >= 64) {
+        x.hi = mant << (sh - 64);
+    } else if (sh > 0) {
+        x.lo = mant << sh;
+        x.hi = mant >> (64 - sh);
+    } else if (sh == 0) {
+        x.lo = mant;
+    } else if (-sh <= 63) {
+        const int r = -sh;
+        x.lo = (mant >> r) + ((mant >> (r - 1)) & 1ull);  // nearest, ties away from zero
+    }
+    if (bits >> 63) {  // negate
+        x.lo = ~x.lo + 1ull;
+        x.hi = ~x.hi + (x.lo == 0ull ? 1ull : 0ull);
+    }
+    return x;
+}
+
+// the sum held in (lo, hi) as a double, rounded to nearest, ties to even
+__device__ __forceinline__ double from_fixed(unsigned long long lo, unsigned long long hi, int S) {
+    const bool neg = (long long)hi < 0;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    if (hi == 0ull && lo == 0ull) return 0.0;
+    int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading bit
+    unsigned long long m;
+    if (p <= 52) {
+        m = lo << (52 - p);
+    } else {
+        const int sh = p - 52;  // 1..74
+        m = sh >= 64 ? hi >> (sh - 64) : (lo >> sh) | (hi << (64 - sh));
+        const int g = sh - 1;   // guard bit position
+        const unsigned long long gbit = g >= 64 ? (hi >> (g - 64)) & 1ull : (lo >> g) & 1ull;
+        const bool sticky = g >= 64 ? (lo != 0ull || (hi & ((1ull << (g - 64)) - 1ull)) != 0ull)
+                                    : (lo & ((1ull << g) - 1ull)) != 0ull;
+        if (gbit && (sticky || (m & 1ull))) ++m;
+        if (m >> 53) {
+            m >>= 1;
+            ++p;
+        }
+    }
+    const unsigned long long bexp = (unsigned long long)(p - S + 1023);
+    const unsigned long long bits = ((unsigned long long)neg << 63) | (bexp << 52) | (m & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
+}
+
+
 // The hash table as the kernels see it.
 struct Table {
     Slot *slots;
     unsigned long long mask;  // capacity - 1 (capacity a power of two)
     int shift;                // 64 - log2(capacity)
-    int *status;              // device: bit 0 = a probe ran past kMaxProbe
+    int *status;              // device: bit 0 = a probe ran past kMaxProbe; bit 1 = a value
+                              // outside the fixed-point range
     unsigned long long *count;  // device: keys inserted
+    unsigned long long *acc = nullptr;  // [2 x capacity] exact sums (lo, hi) of the emit's
+                                        // table mode; nullptr: float64 adds into the slots
+    int fix_shift = 0;                  // units 2^-fix_shift of acc
 };
 
 // Read-only description of a system for the kernels.
@@ -208,6 +286,37 @@ __device__ __forceinline__ bool table_add(const Table &t, unsigned long long key
     return false;
 }
 
+// Add v exactly into the entry `key` (fixed-point sums in t.acc), inserting
+// the key if absent: the sum does not depend on the order of the adds.
+__device__ __forceinline__ bool table_add_exact(const Table &t, unsigned long long key, double v,
+                                                unsigned &inserted) {
+    bool ok = true;
+    const Fix128 f = to_fixed(v, t.fix_shift, ok);
+    if (!ok) atomicOr(t.status, 2);
+    unsigned long long h = hash_slot(key, t.shift);
+    for (int probe = 0; probe < kMaxProbe; ++probe) {
+        if ((probe & 255) == 255 && *(volatile int *)t.status) return false;
+        Slot *s = t.slots + h;
+        unsigned long long cur = __ldcg(&s->key);
+        bool found = cur == key;
+        if (!found && cur == kEmpty) {
+            const unsigned long long old = atomicCAS(&s->key, kEmpty, key);
+            if (old == kEmpty || old == key) {
+                inserted += (old == kEmpty);
+                found = true;
+            }
+        }
+        if (found) {
+            const unsigned long long old = atomicAdd(&t.acc[2 * h], f.lo);
+            atomicAdd(&t.acc[2 * h + 1], f.hi + (old + f.lo < old ? 1ull : 0ull));
+            return true;
+        }
+        h = (h + 1ull) & t.mask;
+    }
+    atomicOr(t.status, 1);
+    return false;
+}
+
 // Find `key`; returns the slot index or -1.
 __device__ __forceinline__ long long table_find(const Table &t, unsigned long long key) {
     unsigned long long h = hash_slot(key, t.shift);
@@ -315,6 +424,10 @@ cudaError_t launch_unrank(const SysDev &d, const unsigned long long *r, unsigned
 
 // sfci_table.cu
 cudaError_t table_clear(Table t, cudaStream_t st);
+// slot values = the exact sums of t.acc rounded to float64 (occupied slots)
+cudaError_t table_finalize_exact(Table t, cudaStream_t st);
+// bits of max |x_k| (non-negative doubles order as integers) into *out (zeroed first)
+cudaError_t max_abs_bits(const double *x, long long n, unsigned long long *out, cudaStream_t st);
 // mark entries with |val| < eps as screened (-0.0)
 cudaError_t table_screen(Table t, double eps, unsigned long long *screened_dev, cudaStream_t st);
 // flag[0] |= 1 if rank is not strictly ascending or some rank >= dim

@@ -54,79 +54,6 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
 
-// ------------------------------------------------------------- exact sums
-// Each sigma entry is accumulated as a 128-bit two's-complement integer in
-// units of 2^-S (S chosen by the host so that no sum leaves the range): an
-// element v = m 2^e (m < 2^53) becomes m 2^(e+S), exactly unless e + S < 0
-// (|v| below 2^(52-S), rounded to the nearest unit).  Integer atomics add
-// them, so the sum is exact and independent of the order of the adds, and one
-// correctly rounded conversion gives the entry's double.
-
-struct Fix128 {
-    unsigned long long lo, hi;
-};
-
-__device__ __forceinline__ Fix128 to_fixed(double v, int S, bool &range_ok) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-    unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
-    int ex = (int)((bits >> 52) & 0x7FF);
-    Fix128 x{0ull, 0ull};
-    if (ex == 0 && mant == 0) return x;
-    if (ex) mant |= 1ull << 52;
-    else ex = 1;
-    const int sh = ex - 1075 + S;  // v = mant 2^(ex-1075)
-    if (sh > 74) {                 // would not fit in 127 bits
-        range_ok = false;
-        return x;
-    }
-    if (sh >= 64) {
-        x.hi = mant << (sh - 64);
-    } else if (sh > 0) {
-        x.lo = mant << sh;
-        x.hi = mant >> (64 - sh);
-    } else if (sh == 0) {
-        x.lo = mant;
-    } else if (-sh <= 63) {
-        const int r = -sh;
-        x.lo = (mant >> r) + ((mant >> (r - 1)) & 1ull);  // nearest, ties away from zero
-    }
-    if (bits >> 63) {  // negate
-        x.lo = ~x.lo + 1ull;
-        x.hi = ~x.hi + (x.lo == 0ull ? 1ull : 0ull);
-    }
-    return x;
-}
-
-// the sum held in (lo, hi) as a double, rounded to nearest, ties to even
-__device__ __forceinline__ double from_fixed(unsigned long long lo, unsigned long long hi, int S) {
-    const bool neg = (long long)hi < 0;
-    if (neg) {
-        lo = ~lo + 1ull;
-        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
-    }
-    if (hi == 0ull && lo == 0ull) return 0.0;
-    int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading bit
-    unsigned long long m;
-    if (p <= 52) {
-        m = lo << (52 - p);
-    } else {
-        const int sh = p - 52;  // 1..74
-        m = sh >= 64 ? hi >> (sh - 64) : (lo >> sh) | (hi << (64 - sh));
-        const int g = sh - 1;   // guard bit position
-        const unsigned long long gbit = g >= 64 ? (hi >> (g - 64)) & 1ull : (lo >> g) & 1ull;
-        const bool sticky = g >= 64 ? (lo != 0ull || (hi & ((1ull << (g - 64)) - 1ull)) != 0ull)
-                                    : (lo & ((1ull << g) - 1ull)) != 0ull;
-        if (gbit && (sticky || (m & 1ull))) ++m;
-        if (m >> 53) {
-            m >>= 1;
-            ++p;
-        }
-    }
-    const unsigned long long bexp = (unsigned long long)(p - S + 1023);
-    const unsigned long long bits = ((unsigned long long)neg << 63) | (bexp << 52) | (m & 0xFFFFFFFFFFFFFull);
-    return __longlong_as_double((long long)bits);
-}
-
 // ------------------------------------------------------------- scan
 
 // exclusive scan of unsigned 32- or 64-bit counts into 64-bit offsets, m

@@ -193,9 +193,43 @@ unsigned stream_grid(unsigned long long work) {
     return (unsigned)g;
 }
 
+__global__ void finalize_exact_kernel(Table t) {
+    const unsigned long long cap = t.mask + 1;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        if (t.slots[i].key != kEmpty) t.slots[i].val = from_fixed(t.acc[2 * i], t.acc[2 * i + 1], t.fix_shift);
+}
+
+__global__ void max_abs_kernel(const double *x, long long n, unsigned long long *out) {
+    unsigned long long m = 0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)__double_as_longlong(x[k]) & 0x7fffffffffffffffull);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 }  // namespace
 
+cudaError_t table_finalize_exact(Table t, cudaStream_t st) {
+    count_launch();
+    finalize_exact_kernel<<<stream_grid(t.mask + 1), kThreads, 0, st>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t max_abs_bits(const double *x, long long n, unsigned long long *out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, 8, st);
+    if (e != cudaSuccess || n <= 0) return e;
+    count_launch();
+    max_abs_kernel<<<stream_grid((unsigned long long)n), kThreads, 0, st>>>(x, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t table_clear(Table t, cudaStream_t st) {
+    if (t.acc) {
+        const cudaError_t e = cudaMemsetAsync(t.acc, 0, size_t(t.mask + 1) * 16, st);
+        if (e != cudaSuccess) return e;
+    }
     count_launch();
     clear_kernel<<<stream_grid(t.mask + 1), kThreads, 0, st>>>(t.slots, t.mask + 1, t.status, t.count);
     return cudaGetLastError();

@@ -301,3 +301,34 @@ def test_lanczos_truncated_cfg0_report(sf, orc):
     print("truncated cfg0 energies gpu-oracle:", eg - eo)
     e_fci = orc.fci_ground_energy(osys)
     assert np.all(eg >= e_fci - 1e-10)
+
+
+def test_sigma_sums_exact_and_repeatable(sf, orc):
+    """Every sigma entry is the exactly rounded sum of its products
+    fl(<D'|H|D> c_D): checked with rational arithmetic on sampled entries, and
+    two calls agree bit for bit."""
+    from fractions import Fraction
+    d = gen.config_system(0)
+    gsys, osys = _systems(sf, orc, d)
+    rng = np.random.default_rng(12)
+    r = np.sort(rng.choice(gsys.dim, size=700, replace=False)).astype(np.uint64)
+    c = rng.normal(size=r.size) * np.exp(rng.normal(size=r.size) * 3)
+    gr1, gv1 = sf.sfci_sigma(gsys, r, c)
+    gr2, gv2 = sf.sfci_sigma(gsys, r, c)
+    k1, v1 = sf.to_u64(gr1), gv1.cpu().numpy()
+    assert np.array_equal(k1, sf.to_u64(gr2))
+    assert np.array_equal(v1.view(np.uint64), gv2.cpu().numpy().view(np.uint64))
+    src, tgt, elem = sf.sfci_debug_excitations(gsys, r)
+    src = src.cpu().numpy()
+    tgt = sf.to_u64(tgt)
+    prod = elem.cpu().numpy() * c[src]          # the float64 products (one rounding each)
+    keep = prod != 0.0
+    tgt, prod = tgt[keep], prod[keep]
+    order = np.argsort(tgt, kind="stable")
+    tgt, prod = tgt[order], prod[order]
+    uk, start = np.unique(tgt, return_index=True)
+    assert np.array_equal(uk, k1)
+    ends = np.append(start[1:], tgt.size)
+    for i in rng.choice(uk.size, size=min(300, uk.size), replace=False):
+        exact = sum((Fraction(float(x)) for x in prod[start[i]:ends[i]]), Fraction(0))
+        assert float(exact) == v1[i], (i, float(exact), v1[i])
