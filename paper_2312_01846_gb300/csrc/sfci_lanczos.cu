@@ -506,7 +506,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         const double held = (double)z->belem.bytes + (double)z->sig_key.bytes + (double)z->sig_val.bytes +
                             (double)z->bovf.bytes + (double)z->bovf_sorted.bytes;
         double avail = 0.85 * ((double)free_b + held);
-        if (z->p.mem_budget > 0) avail = std::min(avail, (double)z->p.mem_budget);
+        if (z->p.mem_budget > 0) avail = std::min(avail, (double)z->p.mem_budget - (double)z->dacc.bytes);
         const double sig_bytes = 1.1 * sig_need * 16.0;
         // for the element regions (a pass's region offsets are 32-bit counts of 4 slots)
         const double budget = std::min(avail - sig_bytes - 2.0 * ovf_cap * 16.0, 4.0 * 4294967295.0 * sizeof(Slot));
