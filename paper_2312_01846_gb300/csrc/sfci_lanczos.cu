@@ -518,7 +518,12 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         const int npass0 = std::max(1, (int)std::min(1e6, std::ceil((double)total_slots * sizeof(Slot) /
                                                                    std::max(budget, 1.0))));
         int npass = npass0;
-        for (;; ++npass) {
+        if (B == 0) {  // every row is dense: no merge pass
+            npass = 0;
+            cuts.assign(1, 0ull);
+            coff.assign(1, 0ull);
+        }
+        for (; B > 0; ++npass) {
             if (npass > (long long)B || budget <= 0.0 || npass > 4 * npass0 + 64) {
                 set_error("not enough device memory for one merge bucket");
                 return SFCI_E_CAPACITY;
