@@ -329,6 +329,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     unsigned hash_cap = 0;
     unsigned long long total_cap = 0;
     unsigned long long Wd = ~0ull;  // rows with at least this many elements are dense
+    double max_rows_all = 0.0;      // dense rows that fit the memory set aside for them
     z->n_dense = 0;
     if (row_mode) {
         // exact element count per target alpha string, then the bucket plan on
@@ -365,6 +366,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             double cap_b = ((double)fb + held_all) / 3.0;
             if (z->p.mem_budget > 0) cap_b = std::min(cap_b, (double)z->p.mem_budget / 3.0);
             const double max_rows = cap_b / ((double)d.cb * 16.0);
+            max_rows_all = max_rows;
             for (int k = 0; k < 16; ++k)
                 if (cnt[k] > 0 && (double)cnt[k] <= max_rows && (d.cb << k) >> k == d.cb) {
                     Wd = d.cb << k;
@@ -378,8 +380,10 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             if ((r = ensure(z->dpos, (nrows + 1) * 8, z->st, "dense index", 1.5))) return r;
             if ((r = ensure(z->drows, K * 8, z->st, "dense rows", 1.5))) return r;
             const size_t need_d = size_t(K) * d.cb * 16;
-            if (z->dacc.bytes < need_d || z->dacc.bytes > 2 * need_d + (size_t(8) << 30)) {
-                // the large buffers hold most of the memory: give it back first (the
+            if (z->dacc.bytes < need_d) {
+                // allocated once at the largest size the selection allows (a new
+                // allocation of this size costs about a second); the large buffers
+                // hold most of the memory, so they are given back first (the
                 // attempt below sizes them again from what is left)
                 SFCI_CUDA(cudaStreamSynchronize(z->st));
                 for (auto *bb : {&z->dacc, &z->belem, &z->sig_key, &z->sig_val, &z->bovf, &z->bovf_sorted}) {
@@ -387,8 +391,9 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                     bb->p = nullptr;
                     bb->bytes = 0;
                 }
+                const size_t full = size_t(std::floor(max_rows_all)) * d.cb * 16;
+                if ((r = ensure(z->dacc, std::max(need_d, full), z->st, "dense sums"))) return r;
             }
-            if ((r = ensure(z->dacc, need_d, z->st, "dense sums", 1.25))) return r;
             SFCI_CUDA(dense_flags(w, nrows, Wd, P<unsigned>(z->dflag), z->st));
             SFCI_CUDA(exclusive_scan(static_cast<const unsigned *>(P<unsigned>(z->dflag)), (long long)nrows,
                                      P<unsigned long long>(z->dpos), z->scan_ws.p, z->st));
