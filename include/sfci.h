@@ -177,13 +177,6 @@ sfci_status sfci_truncate_topk_noalloc(const uint64_t *rank, const double *coef,
 
 /* ---------------------------------------------------------- SFCI Lanczos */
 
-/* sfci_params.flags: sum every alpha row through the merge buckets.  By
- * default the rows that receive at least C(n, n_beta) << k intermediate
- * elements (the smallest k whose rows fit a third of the device memory) are
- * summed in a dense array of C(n, n_beta) exact fixed-point sums each; the
- * results are the same either way (every sum is exact). */
-#define SFCI_NO_DENSE_ROWS 1u
-
 typedef struct sfci_params {
     int64_t n_keep;         /* N_d: entries kept per basis vector (Eq. 11)          */
     int64_t table_capacity; /* slots of sigma's hash table; 0 = sized automatically */
@@ -191,7 +184,7 @@ typedef struct sfci_params {
     double conv_tol;        /* halt when E(n-1) - E(n) < conv_tol (Sec. 2.1); <= 0 off */
     int32_t n_lanczos;      /* N_L: basis vectors per cycle, w_0 included (Sec. 2.1) */
     int32_t max_iter;       /* the step that reaches this sigma count ends its cycle; <= 0 off */
-    uint32_t flags;         /* 0, or SFCI_NO_DENSE_ROWS                              */
+    uint32_t flags;         /* reserved, pass 0                                      */
     int32_t bucket_elems;   /* intermediate elements per merge bucket; 0 = automatic */
     int64_t mem_budget;     /* device bytes this solver's sigma buffers may take;
                                0 = 85 % of what is free (one solver per device)   */

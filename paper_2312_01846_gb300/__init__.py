@@ -21,7 +21,6 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsfci.so")
 SFCI_OK, SFCI_E_INVALID, SFCI_E_CAPACITY, SFCI_E_OVERFLOW = 0, 1, 2, 3
 SFCI_E_CUDA, SFCI_E_TIMEOUT, SFCI_E_NOMEM = 4, 5, 6
 SFCI_FP32_ELEMENTS = 1  # sfci_system_create flag: float32 off-diagonal elements
-SFCI_NO_DENSE_ROWS = 1  # sfci_params.flags: every alpha row through the merge buckets
 
 
 class SfciError(RuntimeError):
@@ -326,13 +325,12 @@ class Lanczos:
 
     def __init__(self, sys: System, init_rank, init_coef, n_keep, n_lanczos=10, max_iter=0,
                  eps_screen=0.0, conv_tol=0.0, table_capacity=0, bucket_elems=0, stream=None,
-                 mem_budget=0, emit_warps=0, eps_element=0.0, ovf_max_log2=0, dense_rows=True):
+                 mem_budget=0, emit_warps=0, eps_element=0.0, ovf_max_log2=0):
         self.sys = sys
         r = _dev(init_rank, torch.int64)
         c = _dev(init_coef, torch.float64)
         self.params = Params(int(n_keep), int(table_capacity), float(eps_screen), float(conv_tol),
-                             int(n_lanczos), int(max_iter), 0 if dense_rows else SFCI_NO_DENSE_ROWS,
-                             int(bucket_elems),
+                             int(n_lanczos), int(max_iter), 0, int(bucket_elems),
                              int(mem_budget), int(emit_warps), int(ovf_max_log2), float(eps_element))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()

@@ -224,7 +224,6 @@ __device__ __forceinline__ unsigned row_bucket(const Buckets &bk, RowCtx rc, uns
         return bk.log2B > 0 ? (unsigned)(mix64(key) >> (64 - bk.log2B)) : 0u;
     }
     if (rc.ns <= 1) return rc.ns ? rc.first : kNoBucket;
-    if (rc.ns == kDenseNs) return kDenseBit | rc.first;
     return rc.first + (unsigned)(((mix64(hb) >> 32) * rc.ns) >> 32);
 }
 
@@ -232,7 +231,6 @@ __device__ __forceinline__ unsigned row_bucket(const Buckets &bk, RowCtx rc, uns
 // the row weights missed it: status 16.
 __device__ __forceinline__ bool ctx_in_pass(const BucketOut &B, RowCtx rc) {
     if (rc.ns == 0xffffffffu) return true;
-    if (rc.ns == kDenseNs) return B.dense_on;
     if (rc.ns == 0) {
         atomicOr(B.status, 16);
         return false;
@@ -251,7 +249,6 @@ __device__ __forceinline__ bool wanted(const EmitOut &o, unsigned long long ha, 
         atomicOr(o.b.status, 16);
         return false;
     }
-    if (b & kDenseBit) return o.b.dense_on;
     return in_pass(o.b, b);
 }
 
@@ -260,7 +257,6 @@ __device__ __forceinline__ bool row_wanted(const EmitOut &o, RowCtx rc, unsigned
                                            unsigned long long hb, unsigned &b) {
     if (kMode != kModeBucket) return true;
     b = row_bucket(o.b.bk, rc, ha, hb);
-    if (is_dense(b)) return o.b.dense_on;
     return in_pass(o.b, b);
 }
 
@@ -356,20 +352,6 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
         if (o.b.eps_elem > 0.0) {  // heat-bath style screen (uniform branch: no FP64 compare when off)
 #pragma unroll
             for (int k = 0; k < kU; ++k) ok[k] = ok[k] && !(fabs(v[k]) < o.b.eps_elem);
-        }
-        if (o.b.dense_on) {  // dense rows: exact adds into their dense array
-#pragma unroll
-            for (int k = 0; k < kU; ++k) {
-                if (!ok[k] || !is_dense(bk[k])) continue;
-                bool fine = true;
-                const Fix128 f = to_fixed(v[k], o.b.fix_shift, fine);
-                if (!fine) atomicOr(o.b.status, 32);
-                unsigned long long *a =
-                    o.b.dense_acc + 2 * ((unsigned long long)(bk[k] & ~kDenseBit) * cb + hb[k]);
-                const unsigned long long old = atomicAdd(a, f.lo);
-                atomicAdd(a + 1, f.hi + (old + f.lo < old ? 1ull : 0ull));
-                ok[k] = false;
-            }
         }
         bool any = false;
 #pragma unroll

@@ -364,12 +364,6 @@ struct BucketOut {
     // between two passes belong to both): a target outside needs no row-map load
     unsigned long long row_lo, row_hi;
     int *status;              // bit 1: overflow list full; bit 4: an element had no bucket
-    // dense rows: their elements are added (exactly, units 2^-fix_shift) into
-    // dense_acc[2 (index C(n, n_beta) + hb)] in the launch with dense_on set
-    // (and skipped in the others)
-    bool dense_on;
-    unsigned long long *dense_acc;
-    int fix_shift;
 };
 
 struct EmitOut {
@@ -385,13 +379,6 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long key) {
 }
 
 constexpr unsigned kNoBucket = 0xffffffffu;
-// Dense rows: alpha rows that many sources reach are summed in a dense
-// fixed-point array (C(n, n_beta) slots per row) instead of merge buckets.
-// Their row-map entry is (dense index << 32) | kDenseNs, and bucket_ab /
-// row_bucket return kDenseBit | dense index for their targets.
-constexpr unsigned kDenseNs = 0x80000000u;
-constexpr unsigned kDenseBit = 0x80000000u;
-__host__ __device__ __forceinline__ bool is_dense(unsigned b) { return b != kNoBucket && (b & kDenseBit); }
 
 // bucket of the determinant (alpha index ha, beta index hb)
 __device__ __forceinline__ unsigned bucket_ab(const Buckets &bk, unsigned long long ha,
@@ -403,7 +390,6 @@ __device__ __forceinline__ unsigned bucket_ab(const Buckets &bk, unsigned long l
     const unsigned long long m = __ldg(&bk.rowmap[ha]);
     const unsigned ns = (unsigned)m, first = (unsigned)(m >> 32);
     if (ns <= 1) return ns ? first : kNoBucket;
-    if (ns == kDenseNs) return kDenseBit | first;
     return first + (unsigned)(((mix64(hb) >> 32) * ns) >> 32);
 }
 
@@ -514,30 +500,6 @@ struct MergeArgs {
     int *status;                        // bit 2: a bucket has too many distinct keys; bit 3: output full;
                                         // bit 5: an element outside the 2^-S fixed-point range
 };
-// dense rows of the bucketed sigma (see kDenseNs): their stream-out
-struct DenseArgs {
-    unsigned long long *acc;            // [2 K C] exact sums
-    const unsigned long long *rows;     // [K] alpha index of each dense row
-    unsigned long long K, C;            // dense rows, beta strings
-    int fix_shift;
-    double eps;                         // screen
-    unsigned long long *out_key;
-    double *out_val;
-    long long out_cap;
-    unsigned long long *out_n;
-    const unsigned long long *tau_bits;
-    unsigned long long *hist;
-    double *sumsq;
-    unsigned long long *n_live, *n_nonzero;
-    int *status;                        // bit 3: output full
-};
-// sigma at the entries of vecs[0..nvec) that lie in dense rows -> sigw (as the merge's probes)
-cudaError_t dense_probes(const Buckets &bk, const VecRef *vecs, double *const *sigw, int nvec,
-                         const unsigned long long *acc, int S, double eps, cudaStream_t st);
-// zero the dense sums at the entries of wa and wb (kept out of the stream)
-cudaError_t dense_zero(const Buckets &bk, const VecRef &wa, const VecRef &wb, unsigned long long *acc,
-                       cudaStream_t st);
-cudaError_t dense_stream(const DenseArgs &A, cudaStream_t st);
 // magnitude bins of |u|: the top 14 bits of the IEEE bit pattern (11 exponent
 // bits, 2 mantissa bits: quarter octaves) of a non-negative double
 constexpr int kHistShift = 50;
@@ -551,24 +513,14 @@ size_t scan_ws_bytes(long long m);
 // exclusive scan of tc, and plan_rows writes the row map and the capacities
 // of B = bstart[T] buckets.
 cudaError_t plan_windows(const unsigned long long *w, const unsigned long long *wpre, unsigned long long nrows,
-                         unsigned long long P, unsigned long long C, unsigned long long Wd, unsigned long long T,
-                         unsigned *tl, unsigned *th, unsigned *tc, cudaStream_t st);
+                         unsigned long long P, unsigned long long C, unsigned long long T, unsigned *tl, unsigned *th,
+                         unsigned *tc, cudaStream_t st);
 cudaError_t plan_rows(const unsigned long long *w, const unsigned long long *wpre, unsigned long long nrows,
-                      unsigned long long P, unsigned long long C, unsigned long long Wd,
-                      const unsigned long long *dpos, const unsigned *tl, const unsigned long long *bstart,
+                      unsigned long long P, unsigned long long C, const unsigned *tl, const unsigned long long *bstart,
                       unsigned long long B, unsigned long long *rowmap, unsigned *cap, cudaStream_t st);
 // out[2k] = first bucket b <= nb with boff[b] >= targets[k], out[2k+1] = boff[b]
 cudaError_t boff_lower_bounds(const unsigned long long *boff, unsigned long long nb,
                               const unsigned long long *targets, int n, unsigned long long *out, cudaStream_t st);
-// dense rows (w >= Wd; Wd = ~0: none): counts[k] = rows with w >= C << k (k < 16);
-// flag[r] = w[r] >= Wd; rows[dpos[r]] = r for the dense rows (dpos: exclusive
-// scan of flag)
-cudaError_t heavy_counts(const unsigned long long *w, unsigned long long nrows, unsigned long long C,
-                         unsigned long long *counts, cudaStream_t st);
-cudaError_t dense_flags(const unsigned long long *w, unsigned long long nrows, unsigned long long Wd, unsigned *flag,
-                        cudaStream_t st);
-cudaError_t dense_rows(const unsigned long long *w, unsigned long long nrows, unsigned long long Wd,
-                       const unsigned long long *dpos, unsigned long long *rows, cudaStream_t st);
 // start4[b] = (boff[b] - boff[lo]) / 4 for b in [lo, hi]
 cudaError_t pass_offsets(const unsigned long long *boff, unsigned lo, unsigned hi, unsigned *start4,
                          cudaStream_t st);

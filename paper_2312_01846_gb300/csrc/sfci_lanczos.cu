@@ -180,8 +180,7 @@ struct sfci_lanczos {
     Buf bcount, belem, bovf, bovf_sorted, tmp_counts, ovf_off, probes, pcount, poff, scan_ws,
         sig_key, sig_val, cand_key, cand_val, weights, rowmap, boff,
         wpre, ptl, pth, pbstart, pcap, pq,  // device bucket plan (row mode)
-        start4,                             // region offsets of the current pass
-        dcounts, dflag, dpos, drows, dacc;  // dense rows: selection, index, alpha index, sums
+        start4;                             // region offsets of the current pass
     long long sig_cap = 0, ovf_cap = 0, cand_cap = 0;
     double *sigw[kMaxVec] = {};
     char *words = nullptr;  // hist[kHistBins] | outn | mlive | ovf_n | cand_n | msumsq | queue | mstatus | nnz | dmin | tau | mark | lock
@@ -196,7 +195,6 @@ struct sfci_lanczos {
     std::vector<double> cut_at;        // truncation cut at each basis index of the last cycle
     std::vector<long long> ovf_at;     // most overflow of a pass at each basis index of the last cycle
     int n_split = 0;                   // pass ranges split because their overflow outgrew the list
-    unsigned long long n_dense = 0;    // dense rows of the current sigma
     unsigned long long stream_prev = 0;  // entries streamed by the previous merge
     unsigned long long *nnz = nullptr;  // device word: non-zero entries off w_i, w_{i-1}
     unsigned long long *tau_w = nullptr, *mark_w = nullptr;  // stream threshold bits, raise mark
@@ -216,8 +214,7 @@ void destroy_lz(sfci_lanczos *z) {
     for (auto *b : {&z->bcount, &z->belem, &z->bovf, &z->bovf_sorted, &z->tmp_counts, &z->ovf_off,
                     &z->probes, &z->pcount, &z->poff, &z->scan_ws, &z->sig_key, &z->sig_val,
                     &z->cand_key, &z->cand_val, &z->weights, &z->rowmap, &z->boff, &z->wpre, &z->ptl,
-                    &z->pth, &z->pbstart, &z->pcap, &z->pq, &z->start4, &z->dcounts, &z->dflag, &z->dpos,
-                    &z->drows, &z->dacc})
+                    &z->pth, &z->pbstart, &z->pcap, &z->pq, &z->start4})
         cudaFree(b->p);
     cudaFree(z->words);
     for (int j = 0; j < kMaxVec; ++j) cudaFree(z->sigw[j]);
@@ -328,9 +325,6 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     unsigned long long B = 0;
     unsigned hash_cap = 0;
     unsigned long long total_cap = 0;
-    unsigned long long Wd = ~0ull;  // rows with at least this many elements are dense
-    double max_rows_all = 0.0;      // dense rows that fit the memory set aside for them
-    z->n_dense = 0;
     if (row_mode) {
         // exact element count per target alpha string, then the bucket plan on
         // the device: light rows packed into windows of half a bucket, heavy
@@ -352,64 +346,8 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         auto *w = P<unsigned long long>(z->weights);
         SFCI_CUDA(exclusive_scan(static_cast<const unsigned long long *>(w), (long long)nrows,
                                  P<unsigned long long>(z->wpre), z->scan_ws.p, z->st));
-        // dense rows: rows with at least C(n, n_beta) << k elements, the smallest
-        // k whose rows fit a 24th of the device memory (at most 16 GB): the
-        // hottest rows only, so the regions keep their passes
-        if (!(z->p.flags & SFCI_NO_DENSE_ROWS)) {
-            if ((r = ensure(z->dcounts, 16 * 8, z->st, "dense row counts"))) return r;
-            unsigned long long cnt[16];
-            SFCI_CUDA(heavy_counts(w, nrows, d.cb, P<unsigned long long>(z->dcounts), z->st));
-            SFCI_CUDA(cudaMemcpyAsync(cnt, z->dcounts.p, sizeof(cnt), cudaMemcpyDeviceToHost, z->st));
-            size_t fb = 0, tb = 0;
-            SFCI_CUDA(cudaMemGetInfo(&fb, &tb));
-            const double held_all = (double)z->dacc.bytes + (double)z->belem.bytes + (double)z->sig_key.bytes +
-                                    (double)z->sig_val.bytes + (double)z->bovf.bytes + (double)z->bovf_sorted.bytes;
-            double cap_b = std::min(((double)fb + held_all) / 24.0, 16e9);
-            if (z->p.mem_budget > 0) cap_b = std::min(cap_b, (double)z->p.mem_budget / 24.0);
-            const double max_rows = cap_b / ((double)d.cb * 16.0);
-            max_rows_all = max_rows;
-            for (int k = 0; k < 16; ++k)
-                if (cnt[k] > 0 && (double)cnt[k] <= max_rows && (d.cb << k) >> k == d.cb) {
-                    Wd = d.cb << k;
-                    z->n_dense = cnt[k];
-                    break;
-                }
-        }
-        if (z->n_dense) {
-            const unsigned long long K = z->n_dense;
-            if ((r = ensure(z->dflag, nrows * 4, z->st, "dense flags", 1.5))) return r;
-            if ((r = ensure(z->dpos, (nrows + 1) * 8, z->st, "dense index", 1.5))) return r;
-            if ((r = ensure(z->drows, K * 8, z->st, "dense rows", 1.5))) return r;
-            const size_t need_d = size_t(K) * d.cb * 16;
-            if (z->dacc.bytes < need_d) {
-                // grown four-fold up to the cap (few reallocations); when the large
-                // buffers hold the memory, they are given back and sized again below
-                const size_t full = size_t(std::floor(max_rows_all)) * d.cb * 16;
-                const size_t want = std::max(need_d, std::min(full, std::max(4 * need_d, size_t(256) << 20)));
-                SFCI_CUDA(cudaStreamSynchronize(z->st));
-                cudaFree(z->dacc.p);
-                z->dacc.p = nullptr;
-                z->dacc.bytes = 0;
-                if (cudaMalloc(&z->dacc.p, want) != cudaSuccess) {
-                    cudaGetLastError();
-                    for (auto *bb : {&z->belem, &z->sig_key, &z->sig_val, &z->bovf, &z->bovf_sorted}) {
-                        cudaFree(bb->p);
-                        bb->p = nullptr;
-                        bb->bytes = 0;
-                    }
-                    if ((r = ensure(z->dacc, want, z->st, "dense sums"))) return r;
-                } else {
-                    z->dacc.bytes = want;
-                }
-            }
-            SFCI_CUDA(dense_flags(w, nrows, Wd, P<unsigned>(z->dflag), z->st));
-            SFCI_CUDA(exclusive_scan(static_cast<const unsigned *>(P<unsigned>(z->dflag)), (long long)nrows,
-                                     P<unsigned long long>(z->dpos), z->scan_ws.p, z->st));
-            SFCI_CUDA(dense_rows(w, nrows, Wd, P<unsigned long long>(z->dpos), P<unsigned long long>(z->drows),
-                                 z->st));
-        }
         // windows: light flag in ptl, heavy bucket count in pth, their sum back in pth
-        SFCI_CUDA(plan_windows(w, P<unsigned long long>(z->wpre), nrows, Pb, d.cb, Wd, T, P<unsigned>(z->ptl),
+        SFCI_CUDA(plan_windows(w, P<unsigned long long>(z->wpre), nrows, Pb, d.cb, T, P<unsigned>(z->ptl),
                                P<unsigned>(z->pth), P<unsigned>(z->pth), z->st));
         SFCI_CUDA(exclusive_scan(static_cast<const unsigned *>(P<unsigned>(z->pth)), (long long)T,
                                  P<unsigned long long>(z->pbstart), z->scan_ws.p, z->st));
@@ -424,8 +362,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if ((r = ensure(z->scan_ws, scan_ws_bytes((long long)std::max({T, nrows, B}) + 1), z->st, "scan workspace",
                         1.5)))
             return r;
-        SFCI_CUDA(plan_rows(w, P<unsigned long long>(z->wpre), nrows, Pb, d.cb, Wd,
-                            z->n_dense ? P<unsigned long long>(z->dpos) : nullptr, P<unsigned>(z->ptl),
+        SFCI_CUDA(plan_rows(w, P<unsigned long long>(z->wpre), nrows, Pb, d.cb, P<unsigned>(z->ptl),
                             P<unsigned long long>(z->pbstart), B, P<unsigned long long>(z->rowmap),
                             P<unsigned>(z->pcap), z->st));
         SFCI_CUDA(round_caps4(P<unsigned>(z->pcap), B, z->st));
@@ -519,7 +456,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         const double held = (double)z->belem.bytes + (double)z->sig_key.bytes + (double)z->sig_val.bytes +
                             (double)z->bovf.bytes + (double)z->bovf_sorted.bytes;
         double avail = 0.85 * ((double)free_b + held);
-        if (z->p.mem_budget > 0) avail = std::min(avail, (double)z->p.mem_budget - (double)z->dacc.bytes);
+        if (z->p.mem_budget > 0) avail = std::min(avail, (double)z->p.mem_budget);
         const double sig_bytes = 1.1 * sig_need * 16.0;
         // for the element regions (a pass's region offsets are 32-bit counts of 4 slots)
         const double budget = std::min(avail - sig_bytes - 2.0 * ovf_cap * 16.0, 4.0 * 4294967295.0 * sizeof(Slot));
@@ -531,12 +468,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         const int npass0 = std::max(1, (int)std::min(1e6, std::ceil((double)total_slots * sizeof(Slot) /
                                                                    std::max(budget, 1.0))));
         int npass = npass0;
-        if (B == 0) {  // every row is dense: no merge pass
-            npass = 0;
-            cuts.assign(1, 0ull);
-            coff.assign(1, 0ull);
-        }
-        for (; B > 0; ++npass) {
+        for (;; ++npass) {
             if (npass > (long long)B || budget <= 0.0 || npass > 4 * npass0 + 64) {
                 set_error("not enough device memory for one merge bucket");
                 return SFCI_E_CAPACITY;
@@ -630,9 +562,6 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         z->nb_log2 = 0;
         while ((1ull << z->nb_log2) < B) ++z->nb_log2;
         z->ms_emit = z->ms_merge = 0.0;
-        if (z->n_dense)  // dense rows: their sums start at zero; the first emit launch adds them
-            SFCI_CUDA(cudaMemsetAsync(z->dacc.p, 0, size_t(z->n_dense) * d.cb * 16, z->st));
-        bool dense_pending = z->n_dense > 0;
         unsigned long long max_ovf = 0;  // most overflow elements of any pass
         unsigned long long ovf_short = 0;  // a range's overflow that the list could not hold
         z->n_split = 0;
@@ -677,13 +606,6 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                 bo.row_hi = lim[1] > 0 ? lim[1] - 1 : 0ull;
             }
             bo.status = z->mstatus;
-            // the first launch also adds the elements of the dense rows (once per
-            // attempt: a pass split later re-emits bucket elements only)
-            bo.dense_on = dense_pending;
-            bo.dense_acc = P<unsigned long long>(z->dacc);
-            bo.fix_shift = fix_shift;
-            if (dense_pending) bo.row_lo = 0, bo.row_hi = ~0ull;
-            dense_pending = false;
             SFCI_CUDA(cudaEventRecord(z->evp[0], z->st));
             SFCI_CUDA(launch_emit_buckets(d, z->wr[i], z->wc[i], n_in, bo, z->st, z->p.emit_warps));
             SFCI_CUDA(cudaEventRecord(z->evp[1], z->st));
@@ -775,65 +697,6 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             z->ms_emit += a, z->ms_merge += b;
         }
         z->n_passes = npass + z->n_split;  // each split adds a pass
-        if (z->n_dense && !ovf_short) {
-            if (dense_pending) {  // no bucket pass ran: the dense rows get a launch of their own
-                BucketOut bd{};
-                bd.bk = bk;
-                bd.count = P<unsigned>(z->bcount);
-                bd.elem = P<Slot>(z->belem);
-                bd.start4 = P<unsigned>(z->start4);
-                bd.ovf = P<Slot>(z->bovf);
-                bd.ovf_n = z->ovf_n;
-                bd.ovf_cap = z->ovf_cap;
-                bd.lo = bd.hi = 0;
-                bd.row_lo = 0, bd.row_hi = ~0ull;
-                bd.status = z->mstatus;
-                bd.dense_on = true;
-                bd.dense_acc = P<unsigned long long>(z->dacc);
-                bd.fix_shift = fix_shift;
-                bd.eps_elem = z->p.eps_element > 0.0 ? z->p.eps_element : 0.0;
-                SFCI_CUDA(cudaEventRecord(z->evp[0], z->st));
-                SFCI_CUDA(launch_emit_buckets(d, z->wr[i], z->wc[i], n_in, bd, z->st, z->p.emit_warps));
-                SFCI_CUDA(cudaEventRecord(z->evp[1], z->st));
-                SFCI_CUDA(cudaEventSynchronize(z->evp[1]));
-                float a = 0.f;
-                cudaEventElapsedTime(&a, z->evp[0], z->evp[1]);
-                z->ms_emit += a;
-            }
-            // sigma at the basis entries in dense rows, the entries of w_i and
-            // w_{i-1} set aside, and the stream-out with the threshold the merge raised
-            SFCI_CUDA(cudaEventRecord(z->evp[1], z->st));
-            std::vector<VecRef> vd(i + 1);
-            for (int j = 0; j <= i; ++j) vd[j] = VecRef{z->wr[j], z->wc[j], z->wn[j]};
-            const double eps_s = z->p.eps_screen > 0.0 ? z->p.eps_screen : 0.0;
-            SFCI_CUDA(dense_probes(bk, vd.data(), z->sigw, i + 1, P<unsigned long long>(z->dacc), fix_shift, eps_s,
-                                   z->st));
-            SFCI_CUDA(dense_zero(bk, vd[i], i > 0 ? vd[i - 1] : VecRef{nullptr, nullptr, 0},
-                                 P<unsigned long long>(z->dacc), z->st));
-            DenseArgs da{};
-            da.acc = P<unsigned long long>(z->dacc);
-            da.rows = P<unsigned long long>(z->drows);
-            da.K = z->n_dense;
-            da.C = d.cb;
-            da.fix_shift = fix_shift;
-            da.eps = eps_s;
-            da.out_key = P<unsigned long long>(z->sig_key);
-            da.out_val = P<double>(z->sig_val);
-            da.out_cap = out_cap;
-            da.out_n = z->outn;
-            da.tau_bits = z->tau_w;
-            da.hist = z->hist;
-            da.sumsq = z->msumsq;
-            da.n_live = z->mlive;
-            da.n_nonzero = z->nnz;
-            da.status = z->mstatus;
-            SFCI_CUDA(dense_stream(da, z->st));
-            SFCI_CUDA(cudaEventRecord(z->evp[2], z->st));
-            SFCI_CUDA(cudaEventSynchronize(z->evp[2]));
-            float b = 0.f;
-            cudaEventElapsedTime(&b, z->evp[1], z->evp[2]);
-            z->ms_merge += b;
-        }
         int hs = 0;
         unsigned long long ho = 0, hl = 0, hz = 0;
         double hq = 0.0;

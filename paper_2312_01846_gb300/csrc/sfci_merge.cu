@@ -190,7 +190,7 @@ __global__ void probe_count_kernel(Buckets bk, VecPackRef vp, SigPack sp, int nv
              k += (long long)gridDim.x * blockDim.x) {
             const unsigned b = bucket_key(bk, w.rank[k]);
             if (b == kNoBucket) sp.p[j][k] = 0.0;  // no element reaches this row
-            else if (!(b & kDenseBit)) atomicAdd(&pcount[b], 1u);  // (dense rows: dense_probe_kernel)
+            else atomicAdd(&pcount[b], 1u);
         }
     }
 }
@@ -203,121 +203,13 @@ __global__ void probe_scatter_kernel(Buckets bk, VecPackRef vp, int nvec, const 
              k += (long long)gridDim.x * blockDim.x) {
             const unsigned long long key = w.rank[k];
             const unsigned b = bucket_key(bk, key);
-            if (b == kNoBucket || (b & kDenseBit)) continue;
+            if (b == kNoBucket) continue;
             const unsigned long long pos = poff[b] + atomicAdd(&pfill[b], 1u);
             Probe p;
             p.key = key;
             p.where = ((unsigned long long)j << 40) | (unsigned long long)k;
             out[pos] = p;
         }
-    }
-}
-
-// ------------------------------------------------------------- dense rows
-// sigma in a dense row r is acc[2 (d C + hb)] (lo, hi; exact sums in units
-// 2^-S), d = the row's dense index, C = beta strings.
-
-// sigma at the basis-vector entries that lie in dense rows (screened as the merge does)
-__global__ void dense_probe_kernel(Buckets bk, VecPackRef vp, SigPack sp, int nvec, const unsigned long long *acc,
-                                   int S, double eps) {
-    for (int j = 0; j < nvec; ++j) {
-        const VecRef w = vp.v[j];
-        for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < w.n;
-             k += (long long)gridDim.x * blockDim.x) {
-            const unsigned long long key = w.rank[k], ha = key / bk.cb;
-            const unsigned long long m = __ldg(&bk.rowmap[ha]);
-            if ((unsigned)m != kDenseNs) continue;
-            const unsigned long long i = (m >> 32) * bk.cb + (key - ha * bk.cb);
-            double v = from_fixed(acc[2 * i], acc[2 * i + 1], S);
-            if (eps > 0.0 && abs_bits(v) < abs_bits(eps)) v = 0.0;
-            sp.p[j][k] = v;
-        }
-    }
-}
-
-// the entries of w_i and w_{i-1} stay out of the stream (u is formed there
-// from the probes): zero them in the dense array once every probe has read it
-__global__ void dense_zero_kernel(Buckets bk, VecRef wa, VecRef wb, unsigned long long *acc) {
-    for (int j = 0; j < 2; ++j) {
-        const VecRef w = j ? wb : wa;
-        for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < w.n;
-             k += (long long)gridDim.x * blockDim.x) {
-            const unsigned long long key = w.rank[k], ha = key / bk.cb;
-            const unsigned long long m = __ldg(&bk.rowmap[ha]);
-            if ((unsigned)m != kDenseNs) continue;
-            const unsigned long long i = (m >> 32) * bk.cb + (key - ha * bk.cb);
-            acc[2 * i] = 0ull;
-            acc[2 * i + 1] = 0ull;
-        }
-    }
-}
-
-// stream the dense entries with |u| >= tau out (u = sigma there), with the
-// merge's histogram, screen, sum of squares and counts; a dense entry whose
-// sum is exactly zero counts as absent
-__global__ void dense_stream_kernel(DenseArgs A) {
-    const unsigned lane = threadIdx.x & 31;
-    const unsigned long long tau_bits = *(volatile const unsigned long long *)A.tau_bits;
-    const bool screen = A.eps > 0.0;
-    const unsigned long long eps_bits = abs_bits(A.eps);
-    const unsigned long long total = A.K * A.C;
-    double sq = 0.0;
-    unsigned long long n_live = 0, n_nonzero = 0;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < total;
-         i0 += stride) {
-        const unsigned long long i = i0 + lane;
-        bool w = false;
-        unsigned long long key = kEmpty;
-        double v = 0.0;
-        unsigned hb = 0x80000000u | lane;
-        if (i < total) {
-            const unsigned long long lo = A.acc[2 * i], hi = A.acc[2 * i + 1];
-            if (lo | hi) {
-                v = from_fixed(lo, hi, A.fix_shift);
-                const unsigned long long ab = abs_bits(v);
-                const bool live = !(screen && ab < eps_bits);
-                n_live += live;
-                if (live && ab != 0ull) {
-                    ++n_nonzero;
-                    sq = __fma_rn(v, v, sq);
-                    w = !(ab < tau_bits);
-                }
-                if (w) {
-                    const unsigned long long d = i / A.C;
-                    key = A.rows[d] * A.C + (i - d * A.C);
-                    hb = (unsigned)(ab >> kHistShift);
-                }
-            }
-        }
-        if (__any_sync(kFull, w)) {
-            const unsigned peers = __match_any_sync(kFull, hb);
-            if (w && (peers & ((1u << lane) - 1u)) == 0)
-                atomicAdd(&A.hist[hb], (unsigned long long)__popc(peers));
-        }
-        const unsigned bal = __ballot_sync(kFull, w);
-        unsigned long long base = 0;
-        if (lane == 0 && bal) base = atomicAdd(A.out_n, (unsigned long long)__popc(bal));
-        base = __shfl_sync(kFull, base, 0);
-        if (w) {
-            const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
-            if ((long long)pos < A.out_cap) {
-                A.out_key[pos] = key;
-                A.out_val[pos] = v;
-            } else {
-                atomicOr(A.status, 8);
-            }
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        sq += __shfl_xor_sync(kFull, sq, o);
-        n_live += __shfl_xor_sync(kFull, n_live, o);
-        n_nonzero += __shfl_xor_sync(kFull, n_nonzero, o);
-    }
-    if (lane == 0) {
-        atomicAdd(A.sumsq, sq);
-        atomicAdd(A.n_live, n_live);
-        atomicAdd(A.n_nonzero, n_nonzero);
     }
 }
 
@@ -776,33 +668,6 @@ cudaError_t sort_probes(const Buckets &bk, unsigned long long nbuckets, const Ve
     if (e != cudaSuccess) return e;
     count_launch();
     probe_scatter_kernel<<<grid_for(mx, 8), 256, 0, st>>>(bk, vp, nvec, poff, pcount, out);
-    return cudaGetLastError();
-}
-
-cudaError_t dense_probes(const Buckets &bk, const VecRef *vecs, double *const *sigw, int nvec,
-                         const unsigned long long *acc, int S, double eps, cudaStream_t st) {
-    VecPackRef vp{};
-    SigPack sp{};
-    long long mx = 1;
-    for (int j = 0; j < nvec; ++j) vp.v[j] = vecs[j], sp.p[j] = sigw[j], mx = vecs[j].n > mx ? vecs[j].n : mx;
-    count_launch();
-    dense_probe_kernel<<<grid_for(mx, 8), 256, 0, st>>>(bk, vp, sp, nvec, acc, S, eps);
-    return cudaGetLastError();
-}
-
-cudaError_t dense_zero(const Buckets &bk, const VecRef &wa, const VecRef &wb, unsigned long long *acc,
-                       cudaStream_t st) {
-    const long long mx = wa.n > wb.n ? wa.n : wb.n;
-    if (mx <= 0) return cudaSuccess;
-    count_launch();
-    dense_zero_kernel<<<grid_for(mx, 8), 256, 0, st>>>(bk, wa, wb, acc);
-    return cudaGetLastError();
-}
-
-cudaError_t dense_stream(const DenseArgs &A, cudaStream_t st) {
-    if (!A.K) return cudaSuccess;
-    count_launch();
-    dense_stream_kernel<<<grid_for((long long)(A.K * A.C), 8), 256, 0, st>>>(A);
     return cudaGetLastError();
 }
 

@@ -18,8 +18,6 @@
 //     table still holds and whose regions overflow far less.
 // Buckets are numbered window by window, so alpha rows and buckets are in the
 // same order and every light bucket is a contiguous rank range.
-// Rows with w >= Wd (dense rows: far more elements than beta strings) get no
-// buckets; their row-map entry holds their index among the dense rows.
 #include <cstdint>
 
 #include "sfci_internal.cuh"
@@ -35,11 +33,11 @@ __device__ __forceinline__ unsigned long long heavy_buckets(unsigned long long w
 
 __global__ void plan_windows_kernel(const unsigned long long *w, const unsigned long long *wpre,
                                     unsigned long long nrows, unsigned long long P, unsigned long long C,
-                                    unsigned long long Wd, unsigned *tl, unsigned *th) {
+                                    unsigned *tl, unsigned *th) {
     for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nrows;
          r += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long wr = w[r];
-        if (!wr || wr >= Wd) continue;  // (dense rows have no buckets)
+        if (!wr) continue;
         const unsigned long long t = wpre[r] / (P / 2);
         if (wr > P / 2) th[t] = (unsigned)heavy_buckets(wr, P, C);
         else tl[t] = 1u;
@@ -59,7 +57,6 @@ __global__ void plan_count_kernel(const unsigned *tl, const unsigned *th, unsign
 // (rows must arrive in window order: P even, windows of P/2)
 __global__ void plan_rows_kernel(const unsigned long long *w, const unsigned long long *wpre,
                                  unsigned long long nrows, unsigned long long P, unsigned long long C,
-                                 unsigned long long Wd, const unsigned long long *dpos,
                                  const unsigned *tl, const unsigned long long *bstart,
                                  unsigned long long *rowmap, unsigned *cap) {
     for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nrows;
@@ -67,10 +64,6 @@ __global__ void plan_rows_kernel(const unsigned long long *w, const unsigned lon
         const unsigned long long wr = w[r];
         if (!wr) {
             rowmap[r] = 0ull;
-            continue;
-        }
-        if (wr >= Wd) {
-            rowmap[r] = (dpos[r] << 32) | kDenseNs;
             continue;
         }
         const unsigned long long t = wpre[r] / (P / 2);
@@ -119,7 +112,7 @@ __global__ void pass_rows_kernel(const unsigned long long *rowmap, unsigned long
          r += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long m = rowmap[r];
         const unsigned ns = (unsigned)m, first = (unsigned)(m >> 32);
-        if (!ns || ns == kDenseNs) continue;
+        if (!ns) continue;
         if ((unsigned long long)first + ns <= lo) atomicMax(&lim[0], r + 1);
         if (first >= hi) atomicMin(&lim[1], r);
     }
@@ -138,35 +131,6 @@ __global__ void round_caps4_kernel(unsigned *cap, unsigned long long nb) {
         cap[b] = (cap[b] + 3u) & ~3u;
 }
 
-// counts[k] = rows with w >= C << k, k < 16
-__global__ void heavy_counts_kernel(const unsigned long long *w, unsigned long long nrows, unsigned long long C,
-                                    unsigned long long *counts) {
-    __shared__ unsigned long long sc[16];
-    if (threadIdx.x < 16) sc[threadIdx.x] = 0;
-    __syncthreads();
-    for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nrows;
-         r += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long wr = w[r];
-        for (int k = 0; k < 16 && wr >= (C << k); ++k) atomicAdd(&sc[k], 1ull);
-    }
-    __syncthreads();
-    if (threadIdx.x < 16 && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sc[threadIdx.x]);
-}
-
-__global__ void dense_flags_kernel(const unsigned long long *w, unsigned long long nrows, unsigned long long Wd,
-                                   unsigned *flag) {
-    for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nrows;
-         r += (unsigned long long)gridDim.x * blockDim.x)
-        flag[r] = w[r] >= Wd ? 1u : 0u;
-}
-
-__global__ void dense_rows_kernel(const unsigned long long *w, unsigned long long nrows, unsigned long long Wd,
-                                  const unsigned long long *dpos, unsigned long long *rows) {
-    for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nrows;
-         r += (unsigned long long)gridDim.x * blockDim.x)
-        if (w[r] >= Wd) rows[dpos[r]] = r;
-}
-
 unsigned grid_of(unsigned long long n) {
     const unsigned long long g = (n + 255) / 256;
     return (unsigned)(g < 16384 ? (g > 0 ? g : 1) : 16384);
@@ -175,27 +139,26 @@ unsigned grid_of(unsigned long long n) {
 }  // namespace
 
 cudaError_t plan_windows(const unsigned long long *w, const unsigned long long *wpre, unsigned long long nrows,
-                         unsigned long long P, unsigned long long C, unsigned long long Wd, unsigned long long T,
-                         unsigned *tl, unsigned *th, unsigned *tc, cudaStream_t st) {
+                         unsigned long long P, unsigned long long C, unsigned long long T, unsigned *tl, unsigned *th,
+                         unsigned *tc, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(tl, 0, size_t(T) * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(th, 0, size_t(T) * 4, st);
     if (e != cudaSuccess) return e;
     count_launch();
-    plan_windows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, wpre, nrows, P, C, Wd, tl, th);
+    plan_windows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, wpre, nrows, P, C, tl, th);
     count_launch();
     plan_count_kernel<<<grid_of(T), 256, 0, st>>>(tl, th, T, tc);
     return cudaGetLastError();
 }
 
 cudaError_t plan_rows(const unsigned long long *w, const unsigned long long *wpre, unsigned long long nrows,
-                      unsigned long long P, unsigned long long C, unsigned long long Wd,
-                      const unsigned long long *dpos, const unsigned *tl,
+                      unsigned long long P, unsigned long long C, const unsigned *tl,
                       const unsigned long long *bstart, unsigned long long B, unsigned long long *rowmap,
                       unsigned *cap, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(cap, 0, size_t(B) * 4, st);
     if (e != cudaSuccess) return e;
     count_launch();
-    plan_rows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, wpre, nrows, P, C, Wd, dpos, tl, bstart, rowmap, cap);
+    plan_rows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, wpre, nrows, P, C, tl, bstart, rowmap, cap);
     return cudaGetLastError();
 }
 
@@ -228,29 +191,6 @@ cudaError_t round_caps4(unsigned *cap, unsigned long long nb, cudaStream_t st) {
     if (!nb) return cudaSuccess;
     count_launch();
     round_caps4_kernel<<<grid_of(nb), 256, 0, st>>>(cap, nb);
-    return cudaGetLastError();
-}
-
-cudaError_t heavy_counts(const unsigned long long *w, unsigned long long nrows, unsigned long long C,
-                         unsigned long long *counts, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(counts, 0, 16 * 8, st);
-    if (e != cudaSuccess) return e;
-    count_launch();
-    heavy_counts_kernel<<<grid_of(nrows), 256, 0, st>>>(w, nrows, C, counts);
-    return cudaGetLastError();
-}
-
-cudaError_t dense_flags(const unsigned long long *w, unsigned long long nrows, unsigned long long Wd, unsigned *flag,
-                        cudaStream_t st) {
-    count_launch();
-    dense_flags_kernel<<<grid_of(nrows), 256, 0, st>>>(w, nrows, Wd, flag);
-    return cudaGetLastError();
-}
-
-cudaError_t dense_rows(const unsigned long long *w, unsigned long long nrows, unsigned long long Wd,
-                       const unsigned long long *dpos, unsigned long long *rows, cudaStream_t st) {
-    count_launch();
-    dense_rows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, nrows, Wd, dpos, rows);
     return cudaGetLastError();
 }
 

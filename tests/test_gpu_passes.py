@@ -68,32 +68,6 @@ def test_passes_and_splits_change_nothing(sf):
         assert np.allclose(c, c1, rtol=1e-12, atol=0)
 
 
-@pytest.mark.parametrize("n_keep", [20_000, 100_000])
-def test_dense_rows_change_nothing(sf, n_keep):
-    """The rows that many sources reach, summed in dense arrays, against the
-    same run with every row through the merge buckets: the same numbers."""
-    d = gen.config_system(2)
-    gsys = sf.System.from_dict(d)
-    steps = 12
-    dense, r1, c1 = _run(sf, gsys, n_keep, steps)
-    plain, r2, c2 = _run(sf, gsys, n_keep, steps, dense_rows=False)
-    print("overflow with / without dense rows", [i["n_overflow"] for i in dense], [i["n_overflow"] for i in plain])
-    print("ms sigma with / without dense rows", [round(i["ms_sigma"], 1) for i in dense],
-          [round(i["ms_sigma"], 1) for i in plain])
-    for key in ("a", "b"):
-        x = np.array([i[key] for i in plain])
-        y = np.array([i[key] for i in dense])
-        assert np.max(np.abs(x - y) / np.maximum(np.abs(x), 1e-300)) < 1e-12, key
-    lx = np.array([i["lambda_min"] for i in plain if i["cycle_end"]])
-    ly = np.array([i["lambda_min"] for i in dense if i["cycle_end"]])
-    assert lx.size == ly.size == 1 and abs(lx[0] - ly[0]) < 1e-12 * abs(lx[0])
-    assert np.array_equal(r1, r2)
-    assert np.allclose(c1, c2, rtol=1e-12, atol=0)
-    # the streamed candidates and the non-zero count agree too (u's norm and the cut)
-    for x, y in zip(plain, dense):
-        assert x["cut"] == y["cut"] and x["n_kept"] == y["n_kept"]
-
-
 def test_overflow_limit_too_small_is_reported(sf):
     """A list limit that no split can satisfy ends the step with SFCI_E_CAPACITY
     and a message naming the overflow list."""
