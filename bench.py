@@ -263,8 +263,8 @@ def precision_study(sf, d, nkeep, n_lanczos, steps, stream):
     lam64, lam32 = out["f64"]["lambda"], out["fp32_elements"]["lambda"]
     out["delta_e_hartree"] = [b - a for a, b in zip(lam64, lam32)]
     out["f64_repeat_delta_e_hartree"] = [b - a for a, b in zip(lam64, out["f64_repeat"]["lambda"])]
-    # cycle ends where two float64 runs agree to 1e-9 Ha (before the truncation has
-    # amplified summation-order differences): there the float32 difference is its own
+    # cycle ends where two float64 runs agree to 1e-9 Ha (all of them: the sigma sums are
+    # exact, so the runs repeat bit for bit): there the float32 difference is its own
     comp = [i for i, r in enumerate(out["f64_repeat_delta_e_hartree"]) if abs(r) < 1e-9]
     out["comparable_cycles"] = comp
     out["max_abs_delta_e_comparable"] = max((abs(out["delta_e_hartree"][i]) for i in comp), default=None)

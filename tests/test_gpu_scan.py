@@ -2,9 +2,10 @@
 instance gives on its own, and, untruncated, what the oracle gives.
 
 The scan only changes where and when each instance's kernels run (its own
-stream, a worker thread); the arithmetic is the solver's.  Energies agree to
-1e-9 Ha untruncated; truncated runs, whose merge order is not fixed, agree to
-1e-8 Ha over the cycles compared.
+stream, a worker thread); the arithmetic is the solver's, with exact sigma
+sums, so the scan repeats the one-at-a-time run.  Energies agree to 1e-9 Ha
+untruncated and, truncated, to 1e-8 Ha over the cycles compared (the bars
+leave room for the float64 dots).
 """
 import numpy as np
 import pytest
