@@ -222,7 +222,8 @@ typedef struct sfci_step_info {
     double ms_step;    /* device time of the whole step                             */
     double ms_emit;    /* of ms_sigma: the emit kernel (all passes)                 */
     double ms_merge;   /* of ms_sigma: overflow sort + merge kernel (all passes)    */
-    double ms_plan;    /* host time planning the merge buckets and buffers          */
+    double ms_plan;    /* wall time of the bucket plan (row weights, device plan,
+                          pass cuts) and of sizing the buffers                  */
     double ms_topk;    /* device time of the truncation (u entries, top-k, sort)    */
     int32_t n_passes;  /* passes over the sources that sigma needed (memory bound, plus
                           passes split because their overflow outgrew the list) */
