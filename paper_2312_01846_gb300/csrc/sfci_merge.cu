@@ -459,8 +459,9 @@ merge_kernel(MergeArgs A) {
                 }
             }
         }
-        __syncthreads();
-        // raise the threshold once the stream passes the mark (one CTA at a time)
+        // raise the threshold once the stream passes the mark (one CTA at a time;
+        // thread 0 looks at the count as it stands, the barrier below publishes
+        // its decision)
         if (tid == 0) {
             s_raise = 0;
             s_bin = -1;
