@@ -459,9 +459,8 @@ merge_kernel(MergeArgs A) {
                 }
             }
         }
-        // raise the threshold once the stream passes the mark (one CTA at a time;
-        // thread 0 looks at the count as it stands, the barrier below publishes
-        // its decision)
+        __syncthreads();
+        // raise the threshold once the stream passes the mark (one CTA at a time)
         if (tid == 0) {
             s_raise = 0;
             s_bin = -1;
