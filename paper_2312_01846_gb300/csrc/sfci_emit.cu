@@ -175,33 +175,28 @@ __device__ __forceinline__ void overflow_append(const BucketOut &B, bool of, con
 // Up to kU elements per lane (ok[k]) are appended to their buckets: the lanes
 // of the warp that share a bucket reserve their slots with one atomic, issued
 // for all k before any result is used, and write one run.
-__device__ __forceinline__ unsigned rec_start(const BucketOut &B, unsigned b) {  // high word, read-only
-    return __ldg(reinterpret_cast<const unsigned *>(B.rec + b) + 1);
-}
-
 __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, const unsigned *bk,
                                             const unsigned long long *tg, const double *v,
                                             unsigned long long *cur) {
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
-    unsigned peers[kU];
-    unsigned long long got[kU];  // the bucket's record before this group's places: start | count
+    unsigned peers[kU], base[kU];
 #pragma unroll
     for (int k = 0; k < kU; ++k) peers[k] = __match_any_sync(kFull, ok[k] ? bk[k] : (0x80000000u | lane));
 #pragma unroll
     for (int k = 0; k < kU; ++k) {
-        got[k] = 0;
-        if (ok[k] && (peers[k] & lt) == 0) got[k] = atomicAdd(&B.rec[bk[k]], (unsigned long long)__popc(peers[k]));
+        base[k] = 0;
+        if (ok[k] && (peers[k] & lt) == 0) base[k] = atomicAdd(&B.count[bk[k]], (unsigned)__popc(peers[k]));
     }
 #pragma unroll
-    for (int k = 0; k < kU; ++k) got[k] = __shfl_sync(kFull, got[k], __ffs(peers[k]) - 1);
+    for (int k = 0; k < kU; ++k) base[k] = __shfl_sync(kFull, base[k], __ffs(peers[k]) - 1);
 #pragma unroll
     for (int k = 0; k < kU; ++k) {
         bool of = false;
         const ulonglong2 sl = make_ulonglong2(tg[k], (unsigned long long)__double_as_longlong(v[k]));
         if (ok[k]) {
-            const unsigned pos = (unsigned)got[k] + __popc(peers[k] & lt);
-            const unsigned long long o0 = (got[k] >> 32) << 2;
-            const unsigned long long o1 = (unsigned long long)rec_start(B, bk[k] + 1) << 2;
+            const unsigned pos = base[k] + __popc(peers[k] & lt);
+            const unsigned long long o0 = (unsigned long long)__ldg(&B.start4[bk[k]]) << 2;
+            const unsigned long long o1 = (unsigned long long)__ldg(&B.start4[bk[k] + 1]) << 2;
             if (pos < o1 - o0) __stcs(reinterpret_cast<ulonglong2 *>(B.elem) + o0 + pos, sl);  // streamed: read once by the merge
             else of = true;
         }
@@ -279,12 +274,11 @@ __device__ __forceinline__ void single_append(const BucketOut &B, unsigned b, co
         tot += __popc(bal);
     }
     if (tot == 0) return;
-    unsigned long long got = 0;
-    if (lane == 0) got = atomicAdd(&B.rec[b], (unsigned long long)tot);
-    got = __shfl_sync(kFull, got, 0);
-    const unsigned base = (unsigned)got;
-    const unsigned long long o0 = (got >> 32) << 2;
-    const unsigned long long cap = ((unsigned long long)rec_start(B, b + 1) << 2) - o0;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&B.count[b], tot);
+    base = __shfl_sync(kFull, base, 0);
+    const unsigned long long o0 = (unsigned long long)__ldg(&B.start4[b]) << 2;
+    const unsigned long long cap = ((unsigned long long)__ldg(&B.start4[b + 1]) << 2) - o0;
     ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(B.elem) + o0;
 #pragma unroll
     for (int k = 0; k < kU; ++k) {

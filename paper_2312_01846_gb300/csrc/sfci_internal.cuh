@@ -350,12 +350,11 @@ struct Buckets {
 
 struct BucketOut {
     Buckets bk;
-    // [B + 1] per bucket: region start from the pass start in units of 4 slots
-    // (high word; regions are multiples of 4 slots) | elements that arrived (low
-    // word), so one atomic returns both
-    unsigned long long *rec;
+    unsigned *count;          // [B] elements that arrived per bucket
     Slot *elem;               // regions of buckets [lo, hi), relative to boff[lo]
     unsigned long long base;  // boff[lo]
+    const unsigned *start4;   // [B + 1]: (boff[b] - boff[lo]) / 4 for b in [lo, hi] (regions are
+                              // multiples of 4 slots): the pass's offsets in half the bytes
     double eps_elem;          // elements with |<D'|H|D> c_D| < eps_elem are not generated (0: off)
     Slot *ovf;                // [ovf_cap]
     unsigned long long *ovf_n;
@@ -469,7 +468,7 @@ struct SigPack {
 struct MergeArgs {
     unsigned lo, hi;
     Buckets bk;
-    const unsigned long long *rec;      // [B + 1] start (high word) | elements that arrived (low word)
+    const unsigned *count;              // [B] elements per bucket
     const Slot *elem;                   // regions of the pass buckets, relative to boff[lo]
     const Slot *ovf_sorted;             // overflow elements sorted by bucket
     const unsigned long long *ovf_off;  // [hi - lo + 1]
@@ -522,8 +521,8 @@ cudaError_t plan_rows(const unsigned long long *w, const unsigned long long *wpr
 // out[2k] = first bucket b <= nb with boff[b] >= targets[k], out[2k+1] = boff[b]
 cudaError_t boff_lower_bounds(const unsigned long long *boff, unsigned long long nb,
                               const unsigned long long *targets, int n, unsigned long long *out, cudaStream_t st);
-// rec[b] = ((boff[b] - boff[lo]) / 4) << 32 (no element arrived yet) for b in [lo, hi]
-cudaError_t pass_offsets(const unsigned long long *boff, unsigned lo, unsigned hi, unsigned long long *rec,
+// start4[b] = (boff[b] - boff[lo]) / 4 for b in [lo, hi]
+cudaError_t pass_offsets(const unsigned long long *boff, unsigned lo, unsigned hi, unsigned *start4,
                          cudaStream_t st);
 // cap[b] rounded up to a multiple of 4
 cudaError_t round_caps4(unsigned *cap, unsigned long long nb, cudaStream_t st);
@@ -534,7 +533,7 @@ cudaError_t exclusive_scan(const unsigned *in, long long m, unsigned long long *
                            cudaStream_t st);
 cudaError_t exclusive_scan(const unsigned long long *in, long long m, unsigned long long *out, void *ws,
                            cudaStream_t st);
-cudaError_t sort_overflow(const Buckets &bk, const unsigned long long *rec, unsigned lo, unsigned nb,
+cudaError_t sort_overflow(const Buckets &bk, const unsigned *count, unsigned lo, unsigned nb,
                           const Slot *ovf, const unsigned long long *ovf_n, long long ovf_cap,
                           unsigned *tmp_counts, unsigned long long *off, void *scan_ws, Slot *out,
                           cudaStream_t st);

@@ -179,7 +179,8 @@ struct sfci_lanczos {
     };
     Buf bcount, belem, bovf, bovf_sorted, tmp_counts, ovf_off, probes, pcount, poff, scan_ws,
         sig_key, sig_val, cand_key, cand_val, weights, rowmap, boff,
-        wpre, ptl, pth, pbstart, pcap, pq;  // device bucket plan (row mode)
+        wpre, ptl, pth, pbstart, pcap, pq,  // device bucket plan (row mode)
+        start4;                             // region offsets of the current pass
     long long sig_cap = 0, ovf_cap = 0, cand_cap = 0;
     double *sigw[kMaxVec] = {};
     char *words = nullptr;  // hist[kHistBins] | outn | mlive | ovf_n | cand_n | msumsq | queue | mstatus | nnz | dmin | tau | mark | lock
@@ -213,7 +214,7 @@ void destroy_lz(sfci_lanczos *z) {
     for (auto *b : {&z->bcount, &z->belem, &z->bovf, &z->bovf_sorted, &z->tmp_counts, &z->ovf_off,
                     &z->probes, &z->pcount, &z->poff, &z->scan_ws, &z->sig_key, &z->sig_val,
                     &z->cand_key, &z->cand_val, &z->weights, &z->rowmap, &z->boff, &z->wpre, &z->ptl,
-                    &z->pth, &z->pbstart, &z->pcap, &z->pq})
+                    &z->pth, &z->pbstart, &z->pcap, &z->pq, &z->start4})
         cudaFree(b->p);
     cudaFree(z->words);
     for (int j = 0; j < kMaxVec; ++j) cudaFree(z->sigw[j]);
@@ -522,7 +523,8 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         z->sig_cap = (long long)(std::min(z->sig_key.bytes, z->sig_val.bytes) / 8);
         ovf_cap = std::min((long long)(std::min(z->bovf.bytes, z->bovf_sorted.bytes) / sizeof(Slot)), ovf_lim);
         z->ovf_cap = ovf_cap;
-        if ((r = ensure(z->bcount, size_t(B + 1) * 8, z->st, "bucket records", 1.5))) return r;
+        if ((r = ensure(z->bcount, size_t(B) * 4, z->st, "bucket counters", 1.5))) return r;
+        if ((r = ensure(z->start4, size_t(B + 1) * 4, z->st, "pass offsets", 1.5))) return r;
         if ((r = ensure(z->probes, size_t(std::max<long long>(totp, 1)) * sizeof(Probe), z->st, "probes"))) return r;
         if ((r = ensure(z->pcount, size_t(B) * 4, z->st, "probe counts", 1.5))) return r;
         if ((r = ensure(z->poff, size_t(B + 1) * 8, z->st, "probe offsets", 1.5))) return r;
@@ -540,6 +542,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         for (int j = 0; j <= i; ++j) vr[j] = VecRef{z->wr[j], z->wc[j], z->wn[j]};
         SFCI_CUDA(sort_probes(bk, B, vr.data(), z->sigw, i + 1, P<unsigned>(z->pcount),
                               P<unsigned long long>(z->poff), z->scan_ws.p, P<Probe>(z->probes), z->st));
+        SFCI_CUDA(cudaMemsetAsync(z->bcount.p, 0, B * 4, z->st));
         SFCI_CUDA(cudaMemsetAsync(z->words, 0, kHistBins * 8 + 1024, z->st));
         // stream threshold (raised by the merge) and its first raise mark: half
         // of the room left for streamed entries once u's entries are set aside
@@ -578,11 +581,11 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             SFCI_CUDA(cudaMemsetAsync(z->ovf_n, 0, 8, z->st));
             BucketOut bo;
             bo.bk = bk;
-            bo.rec = P<unsigned long long>(z->bcount);
+            bo.count = P<unsigned>(z->bcount);
             bo.elem = P<Slot>(z->belem);
             bo.base = rg.olo;
-            // the pass's bucket records: region starts, nothing arrived yet
-            SFCI_CUDA(pass_offsets(P<unsigned long long>(z->boff), lo, hi, P<unsigned long long>(z->bcount), z->st));
+            SFCI_CUDA(pass_offsets(P<unsigned long long>(z->boff), lo, hi, P<unsigned>(z->start4), z->st));
+            bo.start4 = P<unsigned>(z->start4);
             bo.eps_elem = z->p.eps_element > 0.0 ? z->p.eps_element : 0.0;
             bo.ovf = P<Slot>(z->bovf);
             bo.ovf_n = z->ovf_n;
@@ -626,6 +629,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                     SFCI_CUDA(cudaStreamSynchronize(z->st));
                     hs2 &= ~2;  // the list's truncation bit: this range is emitted again in pieces
                     SFCI_CUDA(cudaMemcpyAsync(z->mstatus, &hs2, 4, cudaMemcpyHostToDevice, z->st));
+                    SFCI_CUDA(cudaMemsetAsync(P<unsigned>(z->bcount) + lo, 0, size_t(hi - lo) * 4, z->st));
                     std::vector<unsigned long long> tg, idx, at;
                     for (unsigned j = 1; j < k; ++j) tg.push_back(rg.olo + (rg.ohi - rg.olo) * j / k);
                     SFCI_CUDA(lower_bounds(tg, idx, at));
@@ -648,13 +652,13 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                 ovf_short = std::max(ovf_short, on);
                 break;
             }
-            SFCI_CUDA(sort_overflow(bk, P<unsigned long long>(z->bcount), lo, hi - lo, P<Slot>(z->bovf), z->ovf_n,
+            SFCI_CUDA(sort_overflow(bk, P<unsigned>(z->bcount), lo, hi - lo, P<Slot>(z->bovf), z->ovf_n,
                                     z->ovf_cap, P<unsigned>(z->tmp_counts), P<unsigned long long>(z->ovf_off),
                                     z->scan_ws.p, P<Slot>(z->bovf_sorted), z->st));
             MergeArgs A{};
             A.lo = lo, A.hi = hi;
             A.bk = bk;
-            A.rec = P<unsigned long long>(z->bcount);
+            A.count = P<unsigned>(z->bcount);
             A.elem = P<Slot>(z->belem);
             A.ovf_sorted = P<Slot>(z->bovf_sorted);
             A.ovf_off = P<unsigned long long>(z->ovf_off);

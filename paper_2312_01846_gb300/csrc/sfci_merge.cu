@@ -139,11 +139,11 @@ __global__ void scan_block_kernel(const T *in, long long m, const unsigned long 
 // ------------------------------------------------------------- overflow
 
 // overflow elements per bucket of the pass = max(count - capacity, 0)
-__global__ void ovf_counts_kernel(const unsigned long long *boff, const unsigned long long *rec, unsigned lo,
+__global__ void ovf_counts_kernel(const unsigned long long *boff, const unsigned *count, unsigned lo,
                                   unsigned nb, unsigned *ovc) {
     for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
          b += (long long)gridDim.x * blockDim.x) {
-        const unsigned c = (unsigned)rec[lo + b];
+        const unsigned c = count[lo + b];
         const unsigned cap = (unsigned)(boff[lo + b + 1] - boff[lo + b]);
         ovc[b] = c > cap ? c - cap : 0u;
     }
@@ -302,7 +302,7 @@ merge_kernel(MergeArgs A) {
         if (bi >= A.hi - A.lo) break;
         const unsigned long long tau_bits = s_tau;
         const unsigned b = A.lo + bi;
-        const unsigned cnt = (unsigned)A.rec[b];
+        const unsigned cnt = A.count[b];
         const unsigned long long r0 = A.bk.boff[b];
         const unsigned bcap = (unsigned)(A.bk.boff[b + 1] - r0);
         const unsigned n_main = cnt < bcap ? cnt : bcap;
@@ -635,12 +635,12 @@ cudaError_t exclusive_scan(const unsigned long long *in, long long m, unsigned l
     return exclusive_scan_t(in, m, out, ws, st);
 }
 
-cudaError_t sort_overflow(const Buckets &bk, const unsigned long long *rec, unsigned lo, unsigned nb,
+cudaError_t sort_overflow(const Buckets &bk, const unsigned *count, unsigned lo, unsigned nb,
                           const Slot *ovf, const unsigned long long *ovf_n, long long ovf_cap,
                           unsigned *tmp_counts, unsigned long long *off, void *scan_ws, Slot *out,
                           cudaStream_t st) {
     count_launch();
-    ovf_counts_kernel<<<grid_for(nb, 8), 256, 0, st>>>(bk.boff, rec, lo, nb, tmp_counts);
+    ovf_counts_kernel<<<grid_for(nb, 8), 256, 0, st>>>(bk.boff, count, lo, nb, tmp_counts);
     cudaError_t e = exclusive_scan(tmp_counts, nb, off, scan_ws, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(tmp_counts, 0, size_t(nb) * 4, st);

@@ -118,12 +118,11 @@ __global__ void pass_rows_kernel(const unsigned long long *rowmap, unsigned long
     }
 }
 
-__global__ void pass_offsets_kernel(const unsigned long long *boff, unsigned lo, unsigned hi,
-                                    unsigned long long *rec) {
+__global__ void pass_offsets_kernel(const unsigned long long *boff, unsigned lo, unsigned hi, unsigned *start4) {
     const unsigned long long base = boff[lo];
     for (unsigned long long b = lo + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; b <= hi;
          b += (unsigned long long)gridDim.x * blockDim.x)
-        rec[b] = ((boff[b] - base) >> 2) << 32;
+        start4[b] = (unsigned)((boff[b] - base) >> 2);
 }
 
 __global__ void round_caps4_kernel(unsigned *cap, unsigned long long nb) {
@@ -181,10 +180,10 @@ cudaError_t pass_rows(const unsigned long long *rowmap, unsigned long long nrows
     return cudaGetLastError();
 }
 
-cudaError_t pass_offsets(const unsigned long long *boff, unsigned lo, unsigned hi, unsigned long long *rec,
+cudaError_t pass_offsets(const unsigned long long *boff, unsigned lo, unsigned hi, unsigned *start4,
                          cudaStream_t st) {
     count_launch();
-    pass_offsets_kernel<<<grid_of((unsigned long long)(hi - lo) + 1), 256, 0, st>>>(boff, lo, hi, rec);
+    pass_offsets_kernel<<<grid_of((unsigned long long)(hi - lo) + 1), 256, 0, st>>>(boff, lo, hi, start4);
     return cudaGetLastError();
 }
 
