@@ -132,7 +132,7 @@ __device__ __forceinline__ bool nonzero(double v) {
     return ((unsigned long long)__double_as_longlong(v) << 1) != 0ull;
 }
 
-constexpr int kU = 3;  // elements each lane carries per reservation round
+constexpr int kU = 2;  // elements each lane carries per reservation round
 
 __device__ __forceinline__ bool in_pass(const BucketOut &B, unsigned b) { return b >= B.lo && b < B.hi; }
 
@@ -403,7 +403,7 @@ __device__ __forceinline__ unsigned long long pair_rank(unsigned long long rem, 
 }
 
 template <int kMode>
-__global__ void __launch_bounds__(kEmitThreads, 3)
+__global__ void __launch_bounds__(kEmitThreads, 4)
 emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             const double *__restrict__ in_coef, long long n_in, const EmitOut o) {
     extern __shared__ __align__(16) unsigned char sm[];
