@@ -195,6 +195,8 @@ struct sfci_lanczos {
     std::vector<double> cut_at;        // truncation cut at each basis index of the last cycle
     std::vector<long long> ovf_at;     // most overflow of a pass at each basis index of the last cycle
     int n_split = 0;                   // pass ranges split because their overflow outgrew the list
+    double mult_prev = 0.0;            // elements per distinct sigma entry in the last sigma
+    bool small_buckets = false;        // this sigma is being redone with 1024-element buckets
     unsigned long long stream_prev = 0;  // entries streamed by the previous merge
     unsigned long long *nnz = nullptr;  // device word: non-zero entries off w_i, w_{i-1}
     unsigned long long *tau_w = nullptr, *mark_w = nullptr;  // stream threshold bits, raise mark
@@ -315,8 +317,14 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     const SysDev &d = z->sys->d;
     const long long n_in = z->wn[i];
     const double E = (double)n_in * (double)(d.n_conn + 1);
-    const double per_bucket = z->p.bucket_elems > 0 ? (double)z->p.bucket_elems : 1024.0;
-    const int slots = per_bucket <= 1024.0 ? 2048 : (per_bucket <= 2048.0 ? 4096 : 8192);
+    // elements per merge bucket: 1024 into 2048-slot tables; automatic mode takes
+    // 2048 into the same tables when the previous sigma's entries repeated at
+    // least three times on average (a bucket that still holds more distinct keys
+    // than slots is reported by the merge, and sigma is redone with 1024)
+    const double tau_entry = *tau_io;
+    const bool big_auto = z->p.bucket_elems <= 0 && !z->small_buckets && z->mult_prev >= 3.0;
+    const double per_bucket = z->p.bucket_elems > 0 ? (double)z->p.bucket_elems : (big_auto ? 2048.0 : 1024.0);
+    const int slots = big_auto ? 2048 : (per_bucket <= 1024.0 ? 2048 : (per_bucket <= 2048.0 ? 4096 : 8192));
     const bool row_mode = d.ca <= kMaxRows;
     const auto t_plan0 = std::chrono::steady_clock::now();
     sfci_status r;
@@ -712,6 +720,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         *tau_io = tau;
         if (hs == 0 && !ovf_short) {
             *n_out = ho, *n_live = hl, *n_nonzero = hz, *sumsq = hq;
+            z->mult_prev = E / std::max(1.0, (double)hl);  // intermediate elements per sigma entry
             z->stream_prev = ho;
             z->ovf_used = (long long)max_ovf;
             if ((int)z->ovf_at.size() <= i) z->ovf_at.resize(i + 1, 0);
@@ -743,6 +752,13 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             continue;
         }
         if (hs & 4) {
+            if (big_auto) {  // the larger buckets did not fit the tables: this sigma with 1024
+                z->small_buckets = true;
+                *tau_io = tau_entry;
+                const sfci_status r2 = bucketed_sigma(z, i, tau_io, n_out, n_live, n_nonzero, sumsq);
+                z->small_buckets = false;
+                return r2;
+            }
             set_error("a merge bucket held more distinct entries than its table");
             return SFCI_E_CAPACITY;
         }

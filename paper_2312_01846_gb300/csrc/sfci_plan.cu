@@ -7,13 +7,13 @@
 //   - a light row (0 < w <= Q) joins the light bucket of the window
 //     floor(W(r) / Q) it starts in; the rows of one light bucket are
 //     consecutive and hold at most Q + Q = P elements;
-//   - a heavy row (w > Q) gets ns = min(ceil(w / P), ceil(C / P)) buckets of
-//     its own (C: beta strings), after the light bucket of the window it
+//   - a heavy row (w > Q) gets ns = min(ceil(w / P), ceil(C / 1024)) buckets
+//     of its own (C: beta strings), after the light bucket of the window it
 //     starts in.  It spans more than a window, so the next row starts in a
 //     later one: a window holds light rows, then at most one heavy row.
 //     The split is by a hash of the beta index, so a bucket of a row with
-//     ns = ceil(C / P) can hold no more distinct keys than the beta strings
-//     hashed to it (about P): the rows that many sources reach (w > C, their
+//     ns = ceil(C / 1024) can hold no more distinct keys than the beta strings
+//     hashed to it (about 1024, half the merge table): the rows that many sources reach (w > C, their
 //     keys repeated many times) get fewer, larger buckets, which the merge
 //     table still holds and whose regions overflow far less.
 // Buckets are numbered window by window, so alpha rows and buckets are in the
@@ -25,9 +25,13 @@
 namespace sfci {
 namespace {
 
+// distinct keys a bucket of a row split by the beta hash can hold at most,
+// about: half the slots of the merge table (2048)
+constexpr unsigned long long kKeysPerBucket = 1024;
+
 __device__ __forceinline__ unsigned long long heavy_buckets(unsigned long long wr, unsigned long long P,
                                                          unsigned long long C) {
-    const unsigned long long by_w = (wr + P - 1) / P, by_keys = (C + P - 1) / P;
+    const unsigned long long by_w = (wr + P - 1) / P, by_keys = (C + kKeysPerBucket - 1) / kKeysPerBucket;
     return by_w < by_keys ? by_w : by_keys;
 }
 
