@@ -319,10 +319,11 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     const double E = (double)n_in * (double)(d.n_conn + 1);
     // elements per merge bucket: 1024 into 2048-slot tables; automatic mode takes
     // 2048 into the same tables when the previous sigma's entries repeated at
-    // least three times on average (a bucket that still holds more distinct keys
-    // than slots is reported by the merge, and sigma is redone with 1024)
+    // least 1.5 times on average, i.e. about 1400 distinct keys or fewer per
+    // bucket (a bucket that still holds more distinct keys than slots is
+    // reported by the merge, and sigma is redone with 1024)
     const double tau_entry = *tau_io;
-    const bool big_auto = z->p.bucket_elems <= 0 && !z->small_buckets && z->mult_prev >= 3.0;
+    const bool big_auto = z->p.bucket_elems <= 0 && !z->small_buckets && z->mult_prev >= 1.5;
     const double per_bucket = z->p.bucket_elems > 0 ? (double)z->p.bucket_elems : (big_auto ? 2048.0 : 1024.0);
     const int slots = big_auto ? 2048 : (per_bucket <= 1024.0 ? 2048 : (per_bucket <= 2048.0 ? 4096 : 8192));
     const bool row_mode = d.ca <= kMaxRows;
