@@ -40,7 +40,7 @@ BYTES_PER_ELEMENT = 32  # 16 B intermediate element written + 16 B read back by 
 # DRAM bytes per connected element that ncu measured for emit_kernel + merge_kernel
 # together (dram__bytes_read.sum + dram__bytes_write.sum of one launch each on the same
 # workload at N_d = 5e3, 1.5362e8 elements, one pass); scaled by the elements of a step
-MEASURED_DRAM_BYTES_PER_ELEMENT = (0.100803 + 2.488011 + 2.478259 + 0.004051) * 1e9 / 1.5362e8
+MEASURED_DRAM_BYTES_PER_ELEMENT = (0.042551 + 2.432639 + 2.465470 + 0.004218) * 1e9 / 1.5362e8
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
