@@ -507,17 +507,16 @@ constexpr int kHistBins = 1 << (63 - kHistShift);
 size_t scan_ws_bytes(long long m);
 
 // sfci_plan.cu: merge-bucket plan (row mode) from exact per-row element counts
-// w[nrows] and their exclusive prefix wpre; P elements per light bucket, Ph per
-// heavy-row bucket, C beta strings, T windows of P/2.  plan_windows: tl[t] = a light row starts in window t, tc[t] = tl[t] +
+// w[nrows] and their exclusive prefix wpre; P elements per bucket, C beta
+// strings, T windows of P/2.  plan_windows: tl[t] = a light row starts in window t, tc[t] = tl[t] +
 // buckets of the heavy row starting there (th may alias tc); then bstart =
 // exclusive scan of tc, and plan_rows writes the row map and the capacities
 // of B = bstart[T] buckets.
 cudaError_t plan_windows(const unsigned long long *w, const unsigned long long *wpre, unsigned long long nrows,
-                         unsigned long long P, unsigned long long Ph, unsigned long long C, unsigned long long T,
-                         unsigned *tl, unsigned *th, unsigned *tc, cudaStream_t st);
+                         unsigned long long P, unsigned long long C, unsigned long long T, unsigned *tl, unsigned *th,
+                         unsigned *tc, cudaStream_t st);
 cudaError_t plan_rows(const unsigned long long *w, const unsigned long long *wpre, unsigned long long nrows,
-                      unsigned long long P, unsigned long long Ph, unsigned long long C, const unsigned *tl,
-                      const unsigned long long *bstart,
+                      unsigned long long P, unsigned long long C, const unsigned *tl, const unsigned long long *bstart,
                       unsigned long long B, unsigned long long *rowmap, unsigned *cap, cudaStream_t st);
 // out[2k] = first bucket b <= nb with boff[b] >= targets[k], out[2k+1] = boff[b]
 cudaError_t boff_lower_bounds(const unsigned long long *boff, unsigned long long nb,

@@ -340,8 +340,6 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         // rows split into buckets of their own (sfci_plan.cu)
         const unsigned long long nrows = d.ca;
         const unsigned long long Pb = std::max<unsigned long long>(2, (unsigned long long)per_bucket);
-        // heavy-row buckets twice as large again when entries repeat four times
-        const unsigned long long Ph = big_auto && z->mult_prev >= 4.0 ? 2 * Pb : Pb;
         const unsigned long long T = (unsigned long long)(E / (double)(Pb / 2)) + 2;  // windows
         if ((r = ensure(z->weights, nrows * 8, z->st, "row weights", 1.5))) return r;
         if ((r = ensure(z->rowmap, nrows * 8, z->st, "row map", 1.5))) return r;
@@ -358,7 +356,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         SFCI_CUDA(exclusive_scan(static_cast<const unsigned long long *>(w), (long long)nrows,
                                  P<unsigned long long>(z->wpre), z->scan_ws.p, z->st));
         // windows: light flag in ptl, heavy bucket count in pth, their sum back in pth
-        SFCI_CUDA(plan_windows(w, P<unsigned long long>(z->wpre), nrows, Pb, Ph, d.cb, T, P<unsigned>(z->ptl),
+        SFCI_CUDA(plan_windows(w, P<unsigned long long>(z->wpre), nrows, Pb, d.cb, T, P<unsigned>(z->ptl),
                                P<unsigned>(z->pth), P<unsigned>(z->pth), z->st));
         SFCI_CUDA(exclusive_scan(static_cast<const unsigned *>(P<unsigned>(z->pth)), (long long)T,
                                  P<unsigned long long>(z->pbstart), z->scan_ws.p, z->st));
@@ -373,7 +371,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if ((r = ensure(z->scan_ws, scan_ws_bytes((long long)std::max({T, nrows, B}) + 1), z->st, "scan workspace",
                         1.5)))
             return r;
-        SFCI_CUDA(plan_rows(w, P<unsigned long long>(z->wpre), nrows, Pb, Ph, d.cb, P<unsigned>(z->ptl),
+        SFCI_CUDA(plan_rows(w, P<unsigned long long>(z->wpre), nrows, Pb, d.cb, P<unsigned>(z->ptl),
                             P<unsigned long long>(z->pbstart), B, P<unsigned long long>(z->rowmap),
                             P<unsigned>(z->pcap), z->st));
         SFCI_CUDA(round_caps4(P<unsigned>(z->pcap), B, z->st));

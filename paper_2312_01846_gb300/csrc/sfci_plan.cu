@@ -3,11 +3,11 @@
 // spin-up string" of Sec. 3, with rows too heavy for one bucket split).
 //
 // With W(r) = sum of the counts of the rows before r and windows of Q = P/2
-// elements over W (P: elements per light bucket, Ph >= P per heavy-row bucket):
+// elements over W (P: elements per bucket):
 //   - a light row (0 < w <= Q) joins the light bucket of the window
 //     floor(W(r) / Q) it starts in; the rows of one light bucket are
 //     consecutive and hold at most Q + Q = P elements;
-//   - a heavy row (w > Q) gets ns = min(ceil(w / Ph), ceil(C / 1024)) buckets
+//   - a heavy row (w > Q) gets ns = min(ceil(w / P), ceil(C / 1024)) buckets
 //     of its own (C: beta strings), after the light bucket of the window it
 //     starts in.  It spans more than a window, so the next row starts in a
 //     later one: a window holds light rows, then at most one heavy row.
@@ -36,14 +36,14 @@ __device__ __forceinline__ unsigned long long heavy_buckets(unsigned long long w
 }
 
 __global__ void plan_windows_kernel(const unsigned long long *w, const unsigned long long *wpre,
-                                    unsigned long long nrows, unsigned long long P, unsigned long long Ph,
-                                    unsigned long long C, unsigned *tl, unsigned *th) {
+                                    unsigned long long nrows, unsigned long long P, unsigned long long C,
+                                    unsigned *tl, unsigned *th) {
     for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nrows;
          r += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long wr = w[r];
         if (!wr) continue;
         const unsigned long long t = wpre[r] / (P / 2);
-        if (wr > P / 2) th[t] = (unsigned)heavy_buckets(wr, Ph, C);
+        if (wr > P / 2) th[t] = (unsigned)heavy_buckets(wr, P, C);
         else tl[t] = 1u;
     }
 }
@@ -60,8 +60,8 @@ __global__ void plan_count_kernel(const unsigned *tl, const unsigned *th, unsign
 // rest spills to the overflow list), a one-bucket heavy row exactly its count
 // (rows must arrive in window order: P even, windows of P/2)
 __global__ void plan_rows_kernel(const unsigned long long *w, const unsigned long long *wpre,
-                                 unsigned long long nrows, unsigned long long P, unsigned long long Ph,
-                                 unsigned long long C, const unsigned *tl, const unsigned long long *bstart,
+                                 unsigned long long nrows, unsigned long long P, unsigned long long C,
+                                 const unsigned *tl, const unsigned long long *bstart,
                                  unsigned long long *rowmap, unsigned *cap) {
     for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nrows;
          r += (unsigned long long)gridDim.x * blockDim.x) {
@@ -72,7 +72,7 @@ __global__ void plan_rows_kernel(const unsigned long long *w, const unsigned lon
         }
         const unsigned long long t = wpre[r] / (P / 2);
         if (wr > P / 2) {
-            const unsigned long long ns = heavy_buckets(wr, Ph, C);
+            const unsigned long long ns = heavy_buckets(wr, P, C);
             const unsigned long long first = bstart[t] + tl[t];
             rowmap[r] = (first << 32) | ns;
             unsigned per;
@@ -143,27 +143,26 @@ unsigned grid_of(unsigned long long n) {
 }  // namespace
 
 cudaError_t plan_windows(const unsigned long long *w, const unsigned long long *wpre, unsigned long long nrows,
-                         unsigned long long P, unsigned long long Ph, unsigned long long C, unsigned long long T,
-                         unsigned *tl, unsigned *th,
+                         unsigned long long P, unsigned long long C, unsigned long long T, unsigned *tl, unsigned *th,
                          unsigned *tc, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(tl, 0, size_t(T) * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(th, 0, size_t(T) * 4, st);
     if (e != cudaSuccess) return e;
     count_launch();
-    plan_windows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, wpre, nrows, P, Ph, C, tl, th);
+    plan_windows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, wpre, nrows, P, C, tl, th);
     count_launch();
     plan_count_kernel<<<grid_of(T), 256, 0, st>>>(tl, th, T, tc);
     return cudaGetLastError();
 }
 
 cudaError_t plan_rows(const unsigned long long *w, const unsigned long long *wpre, unsigned long long nrows,
-                      unsigned long long P, unsigned long long Ph, unsigned long long C, const unsigned *tl,
+                      unsigned long long P, unsigned long long C, const unsigned *tl,
                       const unsigned long long *bstart, unsigned long long B, unsigned long long *rowmap,
                       unsigned *cap, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(cap, 0, size_t(B) * 4, st);
     if (e != cudaSuccess) return e;
     count_launch();
-    plan_rows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, wpre, nrows, P, Ph, C, tl, bstart, rowmap, cap);
+    plan_rows_kernel<<<grid_of(nrows), 256, 0, st>>>(w, wpre, nrows, P, C, tl, bstart, rowmap, cap);
     return cudaGetLastError();
 }
 
