@@ -185,7 +185,10 @@ typedef struct sfci_params {
     int32_t n_lanczos;      /* N_L: basis vectors per cycle, w_0 included (Sec. 2.1) */
     int32_t max_iter;       /* the step that reaches this sigma count ends its cycle; <= 0 off */
     uint32_t flags;         /* reserved, pass 0                                      */
-    int32_t bucket_elems;   /* intermediate elements per merge bucket; 0 = automatic */
+    int32_t bucket_elems;   /* intermediate elements per merge bucket; 0 = automatic:
+                               1024, or 2048 once the previous sigma had at least
+                               1.5 elements per distinct entry (a table overflow
+                               then redoes that sigma with 1024)                  */
     int64_t mem_budget;     /* device bytes this solver's sigma buffers may take;
                                0 = 85 % of what is free (one solver per device)   */
     int32_t emit_warps;     /* warps per CTA of the element generator (1..8); 0 = 8 */
