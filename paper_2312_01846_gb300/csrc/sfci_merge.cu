@@ -312,9 +312,9 @@ merge_kernel(MergeArgs A) {
         const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(A.elem) + (r0 - A.bk.boff[A.lo]);
         const ulonglong2 *ovs = reinterpret_cast<const ulonglong2 *>(A.ovf_sorted) + o0;
         const unsigned total = n_main + (unsigned)(o1 - o0);
-        // keys repeat a lot in a bucket past its region or holding more than
-        // twice as many elements as table slots: lanes sharing a key are summed first
-        const bool hot = o1 > o0 || total > 2u * (unsigned)kSlots;
+        // keys repeat a lot in a bucket past its region or holding more
+        // elements than table slots: lanes sharing a key are summed first
+        const bool hot = o1 > o0 || total > (unsigned)kSlots;
         for (unsigned e0 = 0; e0 < total; e0 += kMT * kPre) {
             ulonglong2 x[kPre];
 #pragma unroll
