@@ -235,10 +235,9 @@ def run_reference(a):
 def precision_study(sf, d, nkeep, n_lanczos, steps, stream):
     """The solver from the aufbau determinant with float64 elements (twice) and
     with SFCI_FP32_ELEMENTS: throughput of each and the energy difference at
-    every cycle end.  The second float64 run measures the run-to-run spread
-    (the merge's atomic adds fix no summation order, and the truncation
-    amplifies rounding-level differences), the floor against which the
-    float32 difference is read."""
+    every cycle end.  The second float64 run checks the run-to-run spread: the
+    merge sums every sigma entry exactly (fixed point, rounded once), so two
+    float64 runs repeat bit for bit and the float32 difference is its own."""
     import numpy as np
     import torch
     out = {}

@@ -166,7 +166,10 @@ sfci_status sfci_truncate_topk(const uint64_t *rank, const double *coef, int64_t
  *     clears the parts of the scratch that must start at zero itself.
  *   - The first call on each device looks up the scratch's device address
  *     (with that device current) and caches it; make that first call before
- *     any stream capture.
+ *     any stream capture.  The cache lives as long as the process and does
+ *     not survive a reset of the device (cudaDeviceReset or a new primary
+ *     context): after one, do not call this entry point again in that
+ *     process.
  *   - All calls on one device share the scratch: calls that overlap in time
  *     (other threads, other streams) race and corrupt each other's results.
  *     Serialise them.
@@ -177,6 +180,16 @@ sfci_status sfci_truncate_topk_noalloc(const uint64_t *rank, const double *coef,
 
 /* ---------------------------------------------------------- SFCI Lanczos */
 
+/* sfci_params.flags */
+/* Automatic bucket size (bucket_elems = 0) takes 2048-element merge buckets
+ * into the 2048-slot tables on every sigma, not only once the previous
+ * sigma's entries repeated 1.5 times on average.  A table that cannot hold a
+ * bucket's distinct entries then makes the step redo that sigma with
+ * 1024-element buckets (info->bucket_redo), with the same result.  Slower on
+ * workloads whose entries are mostly distinct; it exists to exercise that
+ * fallback. */
+#define SFCI_LZ_BIG_BUCKETS_ALWAYS 1u
+
 typedef struct sfci_params {
     int64_t n_keep;         /* N_d: entries kept per basis vector (Eq. 11)          */
     int64_t table_capacity; /* slots of sigma's hash table; 0 = sized automatically */
@@ -184,11 +197,12 @@ typedef struct sfci_params {
     double conv_tol;        /* halt when E(n-1) - E(n) < conv_tol (Sec. 2.1); <= 0 off */
     int32_t n_lanczos;      /* N_L: basis vectors per cycle, w_0 included (Sec. 2.1) */
     int32_t max_iter;       /* the step that reaches this sigma count ends its cycle; <= 0 off */
-    uint32_t flags;         /* reserved, pass 0                                      */
+    uint32_t flags;         /* 0 or SFCI_LZ_BIG_BUCKETS_ALWAYS                        */
     int32_t bucket_elems;   /* intermediate elements per merge bucket; 0 = automatic:
                                1024, or 2048 once the previous sigma had at least
                                1.5 elements per distinct entry (a table overflow
-                               then redoes that sigma with 1024)                  */
+                               then redoes that sigma with 1024 and raises that
+                               level to 1.25 times the repetition that failed)    */
     int64_t mem_budget;     /* device bytes this solver's sigma buffers may take;
                                0 = 85 % of what is free (one solver per device)   */
     int32_t emit_warps;     /* warps per CTA of the element generator (1..8); 0 = 8 */
@@ -235,7 +249,8 @@ typedef struct sfci_step_info {
                           below it were not written out; see sfci_lanczos_step)  */
     double cut;        /* |coef| of the N_d-th kept entry of u (0 if fewer kept)    */
     int32_t redo;      /* sigma recomputed because tau hid part of the N_d largest  */
-    int32_t reserved;
+    int32_t bucket_redo; /* sigma recomputed with 1024-element buckets because a
+                            2048-element bucket outgrew its table (automatic size) */
     double pass_budget_gb; /* device memory one pass's element regions may use (GB) */
     double regions_gb;     /* element regions of all buckets (GB): passes ~ this/budget */
     double free_gb;        /* free device memory the plan saw, besides the solver's
@@ -277,7 +292,8 @@ sfci_status sfci_lanczos_load(sfci_lanczos *lz, const uint64_t *rank, const doub
 sfci_status sfci_lanczos_vector(const sfci_lanczos *lz, uint64_t *rank, double *coef,
                                 int64_t cap, int64_t *n);
 /* T and S of the current cycle so far (host, n_lanczos^2 each, row-major,
- * upper triangle j <= i filled). */
+ * upper triangle j <= i filled).  Right after a step that ended a cycle
+ * (info->cycle_end = 1), the T and S that step solved. */
 sfci_status sfci_lanczos_matrices(const sfci_lanczos *lz, double *T, double *S);
 sfci_status sfci_lanczos_destroy(sfci_lanczos *lz);
 
@@ -331,6 +347,19 @@ sfci_status sfci_rdm12_workspace_bytes(const sfci_system *sys, int64_t n, size_t
 sfci_status sfci_rdm12(const sfci_system *sys, const uint64_t *rank, const double *coef, int64_t n,
                        double *rdm1, double *rdm2, double *norm2, void *workspace,
                        size_t ws_bytes, void *stream);
+
+/* The Rayleigh energy of psi from its density matrices and a set of integrals:
+ *   *energy = e_core + (sum_pq h_pq rdm1_pq + 1/2 sum_pqrs g_pqrs rdm2_pqrs) / norm2
+ * (the expectation value of H in the form given above; Sec. 2.1 takes the
+ * ground-state energy as this Rayleigh quotient).  rdm1, rdm2 as written by
+ * sfci_rdm12 and norm2 = <psi|psi> from it; h (n^2) and g (n^4) device float64
+ * in the layout of sfci_system_create, so the integrals may differ from the
+ * system's (the energy as a function of h and g for a fixed psi).  workspace:
+ * device, at least 2456 bytes.  Sums in a fixed order (repeatable).
+ * Synchronises the stream. */
+sfci_status sfci_rdm_energy(int n_orb, const double *rdm1, const double *rdm2, double norm2,
+                            const double *h, const double *g, double e_core, double *energy,
+                            void *workspace, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------- test exports */
 

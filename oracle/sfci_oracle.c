@@ -330,7 +330,7 @@ int64_t or_n_connected(int n, int na, int nb)
 
 /* All determinants reached from (a, b) by one or two electron moves, in a fixed
  * order: alpha singles, beta singles, alpha-alpha doubles, beta-beta doubles,
- * alpha-beta doubles (all single and double excitations). */
+ * alpha-beta doubles (Sec. 4.3, outlook: all single and double excitations). */
 int64_t or_connected(int n, uint64_t a, uint64_t b, uint64_t *oa_out, uint64_t *ob_out)
 {
     int oa[64], va[64], ob[64], vb[64];

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsfci.so")
 SFCI_OK, SFCI_E_INVALID, SFCI_E_CAPACITY, SFCI_E_OVERFLOW = 0, 1, 2, 3
 SFCI_E_CUDA, SFCI_E_TIMEOUT, SFCI_E_NOMEM = 4, 5, 6
 SFCI_FP32_ELEMENTS = 1  # sfci_system_create flag: float32 off-diagonal elements
+SFCI_LZ_BIG_BUCKETS_ALWAYS = 1  # sfci_params flag: 2048-element buckets on every sigma
 
 
 class SfciError(RuntimeError):
@@ -49,7 +50,7 @@ class StepInfo(C.Structure):
                 ("ms_emit", C.c_double), ("ms_merge", C.c_double),
                 ("ms_plan", C.c_double), ("ms_topk", C.c_double),
                 ("n_passes", C.c_int32), ("n_buckets_log2", C.c_int32),
-                ("tau", C.c_double), ("cut", C.c_double), ("redo", C.c_int32), ("reserved", C.c_int32),
+                ("tau", C.c_double), ("cut", C.c_double), ("redo", C.c_int32), ("bucket_redo", C.c_int32),
                 ("pass_budget_gb", C.c_double), ("regions_gb", C.c_double), ("free_gb", C.c_double),
                 ("n_overflow", C.c_int64), ("ms_alloc", C.c_double)]
 
@@ -97,6 +98,8 @@ def lib():
         "sfci_lanczos_destroy": (_i32, [_vp]),
         "sfci_rdm12_workspace_bytes": (_i32, [_vp, _i64, C.POINTER(C.c_size_t)]),
         "sfci_rdm12": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, C.POINTER(_f64), _vp, C.c_size_t, _vp]),
+        "sfci_rdm_energy": (_i32, [_i32, _vp, _vp, _f64, _vp, _vp, _f64, C.POINTER(_f64), _vp, C.c_size_t,
+                                   _vp]),
         "sfci_debug_excitations": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, C.POINTER(_i64), _vp]),
         "sfci_scan_create": (_i32, [C.POINTER(_vp), _i32, C.POINTER(_vp), C.POINTER(Params),
                                     C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_i64), _i32]),
@@ -299,25 +302,40 @@ def sfci_rdm12(sys: System, rank, coef, stream=None):
     return g1, g2, float(nrm.value)
 
 
+def sfci_rdm_energy(g1, g2, norm2, h, g, e_core=0.0, stream=None):
+    """e_core + (sum h g1 + 1/2 sum g g2) / norm2, contracted in the library."""
+    n = g1.shape[0]
+    hh = h.detach().to(device="cuda", dtype=torch.float64).contiguous()
+    gg = g.detach().to(device="cuda", dtype=torch.float64).contiguous()
+    if hh.numel() != n * n or gg.numel() != n ** 4:
+        raise ValueError("h must be (n, n) and g (n, n, n, n) for the RDMs' n")
+    ws = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    e = C.c_double()
+    _check(lib().sfci_rdm_energy(n, _ptr(g1), _ptr(g2), float(norm2), _ptr(hh), _ptr(gg), float(e_core),
+                                 C.byref(e), _ptr(ws), ws.numel(), _stream(stream)), "sfci_rdm_energy")
+    return float(e.value)
+
+
 class RayleighEnergy(torch.autograd.Function):
     """E(h, g) = e_core + (sum h gamma + 1/2 sum g Gamma) / <psi|psi> for a fixed
-    sparse psi; gamma, Gamma come from sfci_rdm12, so dE/dh = gamma / <psi|psi>
-    and dE/dg = Gamma / (2 <psi|psi>).  h: (n, n), g: (n, n, n, n) float64 CUDA
-    tensors; sys fixes n and the electron counts."""
+    sparse psi; gamma, Gamma come from sfci_rdm12 and E from sfci_rdm_energy,
+    so dE/dh = gamma / <psi|psi> and dE/dg = Gamma / (2 <psi|psi>).  h: (n, n),
+    g: (n, n, n, n) float64 CUDA tensors; sys fixes n and the electron counts."""
 
     @staticmethod
     def forward(ctx, h, g, sys, rank, coef, e_core=0.0):
         g1, g2, nrm = sfci_rdm12(sys, rank, coef)
-        d1 = g1 / nrm
-        d2 = g2 * (0.5 / nrm)
-        ctx.save_for_backward(d1, d2)
-        e = (h.to(d1) * d1).sum() + (g.to(d2) * d2).sum() + e_core
-        return e
+        e = sfci_rdm_energy(g1, g2, nrm, h, g, e_core)
+        ctx.nrm = nrm
+        ctx.save_for_backward(g1, g2)
+        return torch.tensor(e, dtype=torch.float64, device=h.device)
 
     @staticmethod
     def backward(ctx, grad):
-        d1, d2 = ctx.saved_tensors
-        return grad * d1, grad * d2, None, None, None, None
+        # dE/dh = gamma / <psi|psi>, dE/dg = Gamma / (2 <psi|psi>): a scale of the
+        # library's RDMs by the incoming gradient
+        g1, g2 = ctx.saved_tensors
+        return grad * (g1 / ctx.nrm), grad * (g2 * (0.5 / ctx.nrm)), None, None, None, None
 
 
 class Lanczos:
@@ -325,12 +343,12 @@ class Lanczos:
 
     def __init__(self, sys: System, init_rank, init_coef, n_keep, n_lanczos=10, max_iter=0,
                  eps_screen=0.0, conv_tol=0.0, table_capacity=0, bucket_elems=0, stream=None,
-                 mem_budget=0, emit_warps=0, eps_element=0.0, ovf_max_log2=0):
+                 mem_budget=0, emit_warps=0, eps_element=0.0, ovf_max_log2=0, flags=0):
         self.sys = sys
         r = _dev(init_rank, torch.int64)
         c = _dev(init_coef, torch.float64)
         self.params = Params(int(n_keep), int(table_capacity), float(eps_screen), float(conv_tol),
-                             int(n_lanczos), int(max_iter), 0, int(bucket_elems),
+                             int(n_lanczos), int(max_iter), int(flags), int(bucket_elems),
                              int(mem_budget), int(emit_warps), int(ovf_max_log2), float(eps_element))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()

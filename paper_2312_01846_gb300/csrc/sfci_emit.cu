@@ -1,8 +1,13 @@
 // sigma = H psi, step 1 (Sec. 2.2): every input entry (D, c_D) generates its
 // intermediate elements (rank(D'), <D'|H|D> c_D) for D' = D and all single and
-// double excitations of D (Sec. 3 / Sec. 4 "all single and double
-// excitations"), and adds them straight into the merge table, so the
-// intermediate elements never travel through HBM.
+// double excitations of D (Sec. 3; Sec. 4.3 notes that every single and
+// double excitation is generated).  Where each element goes depends on the
+// launch: in the solver's bucket mode it is appended as a 16-byte record
+// (rank, value) to its target's merge-bucket region in HBM (past the region's
+// end: to the overflow list), and the merge kernel reduces each bucket in
+// shared memory (sfci_merge.cu); in table mode (the standalone sfci_sigma) it
+// is added exactly into a device-wide hash table; the debug mode writes every
+// element unscaled.
 //
 // One warp owns one input determinant at a time:
 //   a1  rank -> (alpha, beta): division by C(n, n_beta), greedy inverse of Eq. 12
@@ -18,9 +23,12 @@
 //       explicit round-to-nearest intrinsics so no multiply-add is fused;
 //   a5  target index: alpha-major rank = h(alpha') C(n, n_beta) + h(beta');
 //       opposite-spin doubles combine two single-table entries (one IMAD);
-//   a6  element * c_D, exact zeros dropped, hash-added (sfci_internal.cuh).
-// The lanes of the warp stride over the excitations of each class, so a warp
-// issues 32 independent table adds at a time.
+//   a6  element * c_D, exact zeros dropped, then appended to the target's
+//       bucket (warp-aggregated reservation, one atomic per bucket and round)
+//       or added into the table.
+// The lanes of the warp stride over the excitations of each class, two
+// elements per lane per round, so a warp issues 64 independent elements at a
+// time.
 #include "sfci_internal.cuh"
 
 namespace sfci {

@@ -197,6 +197,11 @@ struct sfci_lanczos {
     int n_split = 0;                   // pass ranges split because their overflow outgrew the list
     double mult_prev = 0.0;            // elements per distinct sigma entry in the last sigma
     bool small_buckets = false;        // this sigma is being redone with 1024-element buckets
+    double big_thresh = 1.5;           // mult_prev from which automatic mode tries 2048-element
+                                       // buckets; raised above the level at which a try failed
+    int bucket_redo = 0;               // sigmas of this step redone with 1024-element buckets
+    std::vector<double> T_last, S_last;  // T and S solved at the last cycle end
+    bool just_ended = false;           // the last step ended a cycle
     unsigned long long stream_prev = 0;  // entries streamed by the previous merge
     unsigned long long *nnz = nullptr;  // device word: non-zero entries off w_i, w_{i-1}
     unsigned long long *tau_w = nullptr, *mark_w = nullptr;  // stream threshold bits, raise mark
@@ -323,7 +328,8 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     // bucket (a bucket that still holds more distinct keys than slots is
     // reported by the merge, and sigma is redone with 1024)
     const double tau_entry = *tau_io;
-    const bool big_auto = z->p.bucket_elems <= 0 && !z->small_buckets && z->mult_prev >= 1.5;
+    const bool force_big = (z->p.flags & SFCI_LZ_BIG_BUCKETS_ALWAYS) != 0;
+    const bool big_auto = z->p.bucket_elems <= 0 && !z->small_buckets && (force_big || z->mult_prev >= z->big_thresh);
     const double per_bucket = z->p.bucket_elems > 0 ? (double)z->p.bucket_elems : (big_auto ? 2048.0 : 1024.0);
     const int slots = big_auto ? 2048 : (per_bucket <= 1024.0 ? 2048 : (per_bucket <= 2048.0 ? 4096 : 8192));
     const bool row_mode = d.ca <= kMaxRows;
@@ -693,6 +699,10 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             A.n_nonzero = z->nnz;
             A.queue = z->queue;
             A.status = z->mstatus;
+            // in the automatic 2048-element mode a crowded table gives up early
+            // (the sigma is redone with 1024-element buckets); otherwise the
+            // probe runs until it finds the key or a free slot
+            A.max_probe = big_auto ? 512 : slots;
             SFCI_CUDA(launch_merge(A, slots, z->st));
             SFCI_CUDA(cudaEventRecord(z->evp[2], z->st));
             unsigned long long ovf_here = 0;
@@ -754,6 +764,10 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         }
         if (hs & 4) {
             if (big_auto) {  // the larger buckets did not fit the tables: this sigma with 1024
+                // and no 2048-element try again until entries repeat clearly more
+                // often than they did before this one
+                if (!force_big) z->big_thresh = std::max(z->big_thresh, 1.25 * std::max(z->mult_prev, 1.5));
+                z->bucket_redo += 1;
                 z->small_buckets = true;
                 *tau_io = tau_entry;
                 const sfci_status r2 = bucketed_sigma(z, i, tau_io, n_out, n_live, n_nonzero, sumsq);
@@ -784,6 +798,7 @@ sfci_status load_vector(sfci_lanczos *z, const uint64_t *rank, const double *coe
     z->wn[0] = (long long)std::min<unsigned long long>(hn, (unsigned long long)z->nkeep);
     z->idx = 0;
     z->have_prev = false;
+    z->just_ended = false;
     std::fill(z->T.begin(), z->T.end(), 0.0);
     std::fill(z->S.begin(), z->S.end(), 0.0);
     if (z->wn[0] == 0) {
@@ -820,8 +835,9 @@ sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
         return SFCI_E_INVALID;
     }
     if (params->emit_warps < 0 || params->emit_warps > 8 || params->mem_budget < 0 ||
-        params->bucket_elems < 0 || !(params->eps_element >= 0.0)) {
-        set_error("need 0 <= emit_warps <= 8, mem_budget, bucket_elems, eps_element >= 0");
+        params->bucket_elems < 0 || !(params->eps_element >= 0.0) ||
+        (params->flags & ~SFCI_LZ_BIG_BUCKETS_ALWAYS) != 0) {
+        set_error("need 0 <= emit_warps <= 8, mem_budget, bucket_elems, eps_element >= 0, known flags");
         return SFCI_E_INVALID;
     }
     sfci_lanczos *z = new (std::nothrow) sfci_lanczos();
@@ -909,6 +925,8 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
     std::memset(info, 0, sizeof(*info));
     const SysDev &d = z->sys->d;
     const int i = z->idx, NL = z->NL;
+    z->bucket_redo = 0;
+    z->just_ended = false;
     const long long n_in = z->wn[i];
     SFCI_CUDA(cudaEventRecord(z->ev[0], z->st));
 
@@ -947,6 +965,7 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
         info->n_buckets_log2 = z->nb_log2;
         info->n_elements = n_in * (d.n_conn + 1);
         info->n_sigma = (long long)n_live;
+        info->bucket_redo = z->bucket_redo;
         z->m_prev = (long long)n_live;
         z->nin_prev = n_in;
 
@@ -1099,6 +1118,9 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
         z->have_prev = true;
         z->cycle += 1;
         z->idx = 0;
+        z->T_last = z->T;
+        z->S_last = z->S;
+        z->just_ended = true;
         std::fill(z->T.begin(), z->T.end(), 0.0);
         std::fill(z->S.begin(), z->S.end(), 0.0);
     }
@@ -1134,8 +1156,9 @@ sfci_status sfci_lanczos_matrices(const sfci_lanczos *z, double *T, double *S) {
         set_error("null argument");
         return SFCI_E_INVALID;
     }
-    std::memcpy(T, z->T.data(), z->T.size() * 8);
-    std::memcpy(S, z->S.data(), z->S.size() * 8);
+    const bool ended = z->just_ended && !z->T_last.empty();
+    std::memcpy(T, (ended ? z->T_last : z->T).data(), z->T.size() * 8);
+    std::memcpy(S, (ended ? z->S_last : z->S).data(), z->S.size() * 8);
     return SFCI_OK;
 }
 

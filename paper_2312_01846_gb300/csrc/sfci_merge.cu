@@ -292,6 +292,7 @@ merge_kernel(MergeArgs A) {
     const unsigned long long eps_bits = abs_bits(A.eps);
     for (int sl = tid; sl < kSlots; sl += kMT) keys[sl] = kEmpty, acc_lo[sl] = 0ull, acc_hi[sl] = 0ull, flag[sl] = 0;
     const int S = A.fix_shift;
+    const int max_probe = A.max_probe > 0 && A.max_probe < kSlots ? A.max_probe : kSlots;
     bool range_ok = true;
     if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u), s_tau = *(volatile unsigned long long *)A.tau_bits;
     double sq = 0.0;
@@ -354,7 +355,7 @@ merge_kernel(MergeArgs A) {
                 bool ins = false, found = false;
                 if (act) {
                     h = smem_slot<kSlots>(key, A.bk.rowmap ? 0 : A.bk.log2B);
-                    for (int probe = 0; probe < kSlots; ++probe) {
+                    for (int probe = 0; probe < max_probe; ++probe) {
                         const unsigned long long c = keys[h];
                         if (c == key) {
                             found = true;

@@ -207,6 +207,36 @@ __global__ void norm2_finish(const double *partial, int np, double *out) {
 
 constexpr int kNormBlocks = 152;
 
+// partial[b] = sum over block b's share of k of x[k] y[k] (x, y of length m),
+// fixed grid and order; two launches (h.gamma, then g.Gamma) write disjoint halves
+__global__ void contract_kernel(const double *x, const double *y, long long m, double *partial) {
+    __shared__ double sh[kWarps];
+    double a = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (long long)gridDim.x * blockDim.x)
+        a = __fma_rn(x[i], y[i], a);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kWarps; ++w) t += sh[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+// E = e_core + (sum h gamma + 1/2 sum g Gamma) / norm2 from the two halves of partial
+__global__ void energy_finish(const double *partial, int np, double e_core, double norm2, double *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double one = 0.0, two = 0.0;
+        for (int k = 0; k < np; ++k) one += partial[k];
+        for (int k = 0; k < np; ++k) two += partial[np + k];
+        out[0] = e_core + (one + 0.5 * two) / norm2;
+        out[1] = one;
+        out[2] = two;
+    }
+}
+
 inline size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 unsigned long long rdm_slots(long long m) {
@@ -317,6 +347,33 @@ sfci_status sfci_rdm12(const sfci_system *s, const uint64_t *rank, const double 
         return SFCI_E_INVALID;
     }
     if (norm2) *norm2 = hn;
+    return SFCI_OK;
+}
+
+sfci_status sfci_rdm_energy(int n_orb, const double *rdm1, const double *rdm2, double norm2,
+                            const double *h, const double *g, double e_core, double *energy,
+                            void *workspace, size_t ws_bytes, void *stream) {
+    if (n_orb < 1 || n_orb > 64 || !rdm1 || !rdm2 || !h || !g || !energy || !(norm2 > 0.0)) {
+        set_error("need 1 <= n_orb <= 64, device rdm1, rdm2, h, g, a host energy and norm2 > 0");
+        return SFCI_E_INVALID;
+    }
+    if (!workspace || ws_bytes < size_t(2 * kNormBlocks + 3) * 8) {
+        set_error("workspace below sfci_rdm_energy's 2456 bytes");
+        return SFCI_E_CAPACITY;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double *partial = static_cast<double *>(workspace);
+    double *out = partial + 2 * kNormBlocks;
+    const long long n2 = (long long)n_orb * n_orb;
+    count_launch();
+    contract_kernel<<<kNormBlocks, kThreads, 0, st>>>(h, rdm1, n2, partial);
+    count_launch();
+    contract_kernel<<<kNormBlocks, kThreads, 0, st>>>(g, rdm2, n2 * n2, partial + kNormBlocks);
+    count_launch();
+    energy_finish<<<1, 32, 0, st>>>(partial, kNormBlocks, e_core, norm2, out);
+    SFCI_CUDA(cudaGetLastError());
+    SFCI_CUDA(cudaMemcpyAsync(energy, out, 8, cudaMemcpyDeviceToHost, st));
+    SFCI_CUDA(cudaStreamSynchronize(st));
     return SFCI_OK;
 }
 

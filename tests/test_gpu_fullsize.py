@@ -2,6 +2,9 @@
 and the benchmark's 1e6), in the launch configuration bench.py times, checked
 on sampled entries the oracle computes one by one.
 
+At N_d = 1e5 the step's a_i and b_i are checked against the oracle's sigma
+pulled at every entry of w_i and w_{i-1} (within 1e-11 sum_k |w_k| A_k).
+
 After a step i the solver holds w_{i+1} = normalise(top_{N_d}(u)) with
 u = sigma_i - a w_i - b w_{i-1} (Eqs. 10-11).  For sampled ranks k:
   - kept k: w_{i+1}[k] = u_k / ||top(u)||, so w_{i+1}[k] / u_k is one common
@@ -58,6 +61,15 @@ def test_step_sampled_against_oracle(sf, orc, n_keep, steps):
     (ri, ci), (rm, cm), (ro, co) = vecs[i], vecs[i - 1], vecs[i + 1]
     a, b = info["a"], info["b"]
     rng = np.random.default_rng(7)
+    if n_keep <= 100_000:
+        # a_i = <w_i|sigma_i> and b_i = <w_{i-1}|sigma_i> (Eq. 10) from the
+        # oracle's sigma pulled at every entry of w_i and of w_{i-1}
+        for (rv, cv, got, name) in ((ri, ci, a, "a"), (rm, cm, b, "b")):
+            s, asum, _ = orc.sigma_entries(osys, ri, ci, rv)
+            want = float(np.dot(cv, s))
+            bound = 1e-11 * float(np.dot(np.abs(cv), asum))
+            print(f"N_d={n_keep}: {name} gpu {got!r} oracle {want!r} bound {bound:.3g}")
+            assert abs(got - want) <= bound, (name, got, want, bound)
 
     def u_of(keys):
         s, _, _ = orc.sigma_entries(osys, ri, ci, keys)

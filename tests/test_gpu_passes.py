@@ -81,3 +81,25 @@ def test_overflow_limit_too_small_is_reported(sf):
     lz.close()
     assert ei.value.status == sf.SFCI_E_CAPACITY
     assert "overflow list" in str(ei.value)
+
+
+def test_big_bucket_fallback_is_exact(sf):
+    """Automatic bucket size forced to 2048 elements per 2048-slot table on
+    every sigma (SFCI_LZ_BIG_BUCKETS_ALWAYS).  From the aufbau determinant
+    sigma's entries are all distinct, so some tables cannot hold their
+    bucket's keys: those sigmas are redone with 1024-element buckets
+    (info["bucket_redo"]).  The run must equal, bit for bit, a run with
+    1024-element buckets throughout (exact sums, exact top-N_d)."""
+    d = gen.config_system(2)
+    gsys = sf.System.from_dict(d)
+    n_keep, steps = 20_000, 12
+    ref, r1, c1 = _run(sf, gsys, n_keep, steps, bucket_elems=1024)
+    big, r2, c2 = _run(sf, gsys, n_keep, steps, flags=sf.SFCI_LZ_BIG_BUCKETS_ALWAYS)
+    redo = [i["bucket_redo"] for i in big]
+    print("sigmas redone with 1024-element buckets per step:", redo)
+    assert sum(redo) >= 1
+    assert all(i["bucket_redo"] == 0 for i in ref)
+    for key in ("a", "b", "lambda_min", "n_sigma", "n_kept"):
+        assert [i[key] for i in ref] == [i[key] for i in big], key
+    assert np.array_equal(r1, r2)
+    assert np.array_equal(c1.view(np.uint64), c2.view(np.uint64))

@@ -70,6 +70,7 @@ def test_rdm_cfg4_energy_and_finite_differences(sf, orc):
     h_t = torch.tensor(d["h"], device="cuda", requires_grad=True)
     g_t = torch.tensor(d["g"], device="cuda", requires_grad=True)
     e = sf.RayleighEnergy.apply(h_t, g_t, gsys, r, c, 0.0)
+    assert abs(e.item() - e_or) < 1e-9  # the library's contraction (sfci_rdm_energy)
     e.backward()
     gh, gg = h_t.grad.cpu().numpy(), g_t.grad.cpu().numpy()
     rng = np.random.default_rng(43)
