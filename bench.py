@@ -57,6 +57,9 @@ def parse():
                    help="input determinants in the CPU oracle's timed sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-workloads", action="store_true",
+                   help="skip the rows of the other workloads (8-orbital full space, Hubbard ring, "
+                        "N_d = 1e5, RDM pass) and the pipe-rate probes")
     p.add_argument("--bucket-elems", type=int, default=0,
                    help="intermediate elements per merge bucket (0 = automatic)")
     p.add_argument("--table-capacity", type=int, default=0,
@@ -86,13 +89,13 @@ def workload_name(a):
     return f"sfci-28o-7a7b-L200-clustered-Nd{a.nkeep:.0e}-NL{a.nlanczos}".replace("+0", "")
 
 
-def config(a, extra=None):
-    c = {"workload": workload_name(a), "n_orb": 28, "n_alpha": 7, "n_beta": 7,
-         "n_factors": 200, "n_keep": a.nkeep, "n_lanczos": a.nlanczos,
-         "start": "aufbau determinant", "integrals": "seeded synthetic (seed 2)"}
-    if extra:
-        c.update(extra)
-    return c
+def config(a, world=1):
+    """The workload; the same dictionary on both arms."""
+    return {"workload": workload_name(a), "n_orb": 28, "n_alpha": 7, "n_beta": 7,
+            "n_factors": 200, "n_keep": a.nkeep, "n_lanczos": a.nlanczos,
+            "start": "aufbau determinant", "integrals": "seeded synthetic (seed 2)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "no flush: each step's element regions (hundreds of GB at N_d = 1e6) exceed the 129 MB L2"}
 
 
 def reduce_over_ranks(ms, elements, dist=None, device="cuda"):
@@ -192,6 +195,8 @@ def oracle_sample(n_src):
 
 
 def time_oracle(n_src, threads=None):
+    """sigma of the first n_src determinants of a near-aufbau vector by the
+    oracle on `threads` host threads: (elements/s, elements, seconds, threads)."""
     import oracle
     osys, r, c = oracle_sample(n_src)
     nt = threads or oracle.n_threads()
@@ -220,11 +225,11 @@ def run_reference(a):
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * t_tot / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config(a, {"sample": f"sigma of the first {max(10, a.cpu_sample // 5)} "
-                                           f"determinants of a near-aufbau vector"}),
+            "config": config(a, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
-                             "sample": f"{a.steps} x sigma of {max(10, a.cpu_sample // 5)} "
-                                       f"input determinants (plain C, OpenMP)"},
+                             "sample": f"each step: sigma of the first {max(10, a.cpu_sample // 5)} "
+                                       f"determinants of a near-aufbau vector of the workload "
+                                       f"(plain C, OpenMP)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -379,6 +384,94 @@ def screen_study(sf, d, nkeep, n_lanczos, steps, stream, eps_list):
     return out
 
 
+def solver_row(sf, d, name, nkeep, n_lanczos, warmup, steps, stream, note):
+    """One SURVEY-style measurement row: the solver from the aufbau determinant,
+    `warmup` untimed steps, then `steps` timed with CUDA events on the solver's
+    stream.  Enumerated and generated (non-zero) elements per second, Lanczos
+    steps per second, mean sigma time and the cycle-end energies."""
+    import numpy as np
+    import torch
+    gsys = sf.System.from_dict(d)
+    lz = sf.Lanczos(gsys, np.array([0], dtype=np.uint64), np.array([1.0]), nkeep, n_lanczos,
+                    stream=stream)
+    for _ in range(warmup):
+        lz.step()
+    torch.cuda.synchronize()
+    l0 = sf.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = [lz.step() for _ in range(steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = sf.kernel_launches() - l0
+    lz.close()
+    gsys.close()
+    el = sum(i["n_elements"] for i in infos)
+    nz = sum(i["n_emitted"] for i in infos)
+    return {"workload": name, "note": note, "n_keep": nkeep, "n_lanczos": n_lanczos,
+            "warmup": warmup, "steps": steps, "ms_per_step": ms / steps,
+            "lanczos_steps_per_s": steps / (ms * 1e-3),
+            "elements_per_s": el / (ms * 1e-3), "nonzero_elements_per_s": nz / (ms * 1e-3),
+            "elements_per_step": el / steps, "nonzero_elements_per_step": nz / steps,
+            "ms_sigma_mean": statistics.mean(i["ms_sigma"] for i in infos),
+            "n_in_last": infos[-1]["n_in"], "passes_max": max(i["n_passes"] for i in infos),
+            "gpu_launches_per_step": launches / steps,
+            "lambda_cycle_ends": [i["lambda_min"] for i in infos if i["cycle_end"]]}
+
+
+def rdm_row(sf, stream, nkeep=300_000, grow_steps=12, reps=3):
+    """20 orbitals 5a/5b (L = 64): the solver grows a sparse vector of N_d = 3e5
+    determinants from the aufbau determinant, then sfci_rdm12 runs on it
+    (one pass of the excitation generator over the vector, 1- and 2-RDM by
+    atomics), timed with CUDA events; elements = entries x (n_conn + 1)."""
+    import numpy as np
+    import torch
+
+    import gen
+    d = gen.config_system(4)
+    gsys = sf.System.from_dict(d)
+    lz = sf.Lanczos(gsys, np.array([0], dtype=np.uint64), np.array([1.0]), nkeep, 10, stream=stream)
+    for _ in range(grow_steps):
+        lz.step()
+    r, c = lz.vector()
+    lz.close()
+    sf.sfci_rdm12(gsys, r, c, stream=stream)  # warm-up
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        g1, g2, nrm = sf.sfci_rdm12(gsys, r, c, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    el = r.numel() * (gsys.n_conn + 1)
+    h = torch.tensor(d["h"], device="cuda")
+    g = torch.tensor(d["g"], device="cuda")
+    e = sf.sfci_rdm_energy(g1, g2, nrm, h, g, 0.0)
+    gsys.close()
+    return {"workload": "rdm12-20o-5a5b-L64-Nd3e5", "n_det": int(r.numel()), "ms_per_pass": ms,
+            "elements_per_s": el / (ms * 1e-3), "elements_per_pass": el, "energy": e,
+            "note": "sigma-generator pass over a 3e5-determinant SFCI vector (12 steps from the aufbau "
+                    "determinant), 1- and 2-RDM accumulated with float64 atomics"}
+
+
+def pipe_rates(sf):
+    """Lane operations per second and per SM per clock of the pipe operations
+    the sigma kernels depend on (sfci_debug_pipe_rate)."""
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    out = {}
+    for k in sf.PIPE_KINDS:
+        iters = 1 << 12 if k.startswith("fp64") else 1 << 14
+        r = sf.pipe_rate(k, iters)
+        out[k] = {"ops_per_s": r, "per_sm_per_clk_at_2070_mhz": r / sms / 2.07e9}
+    return out
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -404,10 +497,12 @@ def run_ours(a):
     lz = sf.Lanczos(gsys, np.array([0], dtype=np.uint64), np.array([1.0]), a.nkeep, a.nlanczos,
                     table_capacity=a.table_capacity, bucket_elems=a.bucket_elems, stream=stream,
                     emit_warps=a.emit_warps)
+
     def brief(i):
         return {k: i[k] for k in ("n_in", "n_sigma", "n_passes", "ms_plan", "ms_emit", "ms_merge",
-                                  "ms_topk", "ms_step", "redo", "tau", "cut", "pass_budget_gb",
-                                  "regions_gb", "free_gb", "n_overflow", "ms_alloc")}
+                                  "ms_topk", "ms_step", "redo", "bucket_redo", "tau", "cut",
+                                  "pass_budget_gb", "regions_gb", "free_gb", "n_overflow", "ms_alloc",
+                                  "n_emitted")}
 
     warm = []
     for _ in range(a.warmup):
@@ -455,52 +550,76 @@ def run_ours(a):
                 "passes": max(i["n_passes"] for i in infos),
                 "buckets_log2": max(i["n_buckets_log2"] for i in infos),
                 "elements_per_launch": el_per_launch,
+                "nonzero_elements_per_launch": statistics.mean(i["n_emitted"] for i in infos),
                 "sigma_share_of_step": sum(i["ms_sigma"] for i in infos) / ms}
 
-    # end to end through the public API with host buffers: per step, the input
-    # vector goes host -> device, the solver restarts from it, runs one step,
-    # and the next basis vector and the step's scalars come back to the host
+    # end to end through the public API with host buffers, chained: each step
+    # copies its input vector host -> device, restarts the solver from it
+    # (sfci_lanczos_load), runs one step, and copies the next basis vector back
+    # to the host, where it is the next step's input
     e2e = None
     if not a.no_e2e:
         r_dev, c_dev = lz.vector()
-        h_r = r_dev.cpu().pin_memory()
-        h_c = c_dev.cpu().pin_memory()
-        out_r = torch.empty(a.nkeep, dtype=torch.int64).pin_memory()
-        out_c = torch.empty(a.nkeep, dtype=torch.float64).pin_memory()
+        cap = a.nkeep
+        h_r = torch.empty(cap, dtype=torch.int64).pin_memory()
+        h_c = torch.empty(cap, dtype=torch.float64).pin_memory()
+        h_r[: r_dev.numel()].copy_(r_dev)
+        h_c[: c_dev.numel()].copy_(c_dev)
+        n_cur = r_dev.numel()
         n_e2e = max(1, min(a.steps, 5))
         barrier()
         t0 = time.perf_counter()
         el2 = 0
         h2d = d2h = 0
         for _ in range(n_e2e):
-            dr = h_r.to("cuda", non_blocking=True)
-            dc = h_c.to("cuda", non_blocking=True)
+            dr = h_r[:n_cur].to("cuda", non_blocking=True)
+            dc = h_c[:n_cur].to("cuda", non_blocking=True)
             lz.load(dr, dc)
             info = lz.step()
             el2 += info["n_elements"]
             nr, nc = lz.vector()
-            out_r[: nr.numel()].copy_(nr, non_blocking=True)
-            out_c[: nc.numel()].copy_(nc, non_blocking=True)
+            h_r[: nr.numel()].copy_(nr, non_blocking=True)
+            h_c[: nc.numel()].copy_(nc, non_blocking=True)
             torch.cuda.current_stream().synchronize()
-            h2d += 16 * h_r.numel()
+            h2d += 16 * n_cur
             d2h += 16 * nr.numel() + 152
+            n_cur = nr.numel()
         barrier()
         dt = time.perf_counter() - t0
         e2e = {"value": el2 / dt, "unit": UNIT, "h2d_bytes_per_step": h2d // n_e2e,
                "d2h_bytes_per_step": d2h // n_e2e, "steps": n_e2e,
-               "note": "restart from a host vector + one step + next vector to host"}
+               "note": "chained: host vector in, restart + one step, next vector to the host as the "
+                       "next step's input (wall clock)"}
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         v, nel, dt, nt = time_oracle(a.cpu_sample)
+        v1, nel1, dt1, _ = time_oracle(max(10, a.cpu_sample // 10), threads=1)
         cpu = {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle",
                "sample": f"sigma of {a.cpu_sample} input determinants of a near-aufbau "
-                         f"vector of the workload ({nel} elements, {dt:.1f} s)"}
+                         f"vector of the workload ({nel} elements, {dt:.1f} s)",
+               "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                 "sample": f"sigma of {max(10, a.cpu_sample // 10)} input determinants "
+                                           f"({nel1} elements, {dt1:.1f} s)"}}
 
     last_lambda = [i["lambda_min"] for i in infos if i["cycle_end"]]
     # the studies below build their own solvers: free this one's device memory first
     lz.close()
     torch.cuda.synchronize()
+
+    workloads = None
+    if rank == 0 and not a.no_workloads:
+        workloads = {
+            "cfg0": solver_row(sf, gen.config_system(0), "sfci-8o-4a4b-L16-full-space", 4900, 10, 3, 30,
+                               stream, "whole space (N_d = dim = 4900): launch-latency floor of a step"),
+            "cfg1": solver_row(sf, gen.config_system(1), "hubbard-ring-12-6a6b-U4-Nd2e4", 20_000, 10, 0, 40,
+                               stream, "40 steps from the aufbau determinant; most enumerated elements are "
+                                       "zero products, nonzero_elements_per_s counts those generated"),
+            "cfg2_nd1e5": solver_row(sf, d, "sfci-28o-7a7b-L200-clustered-Nd1e5-NL10", 100_000, 10, 4, 16,
+                                     stream, "same system as the headline at N_d = 1e5"),
+            "cfg4_rdm": rdm_row(sf, stream),
+        }
+    issue = pipe_rates(sf) if rank == 0 and not a.no_workloads else None
 
     precision = None
     if rank == 0 and not a.no_precision:
@@ -515,12 +634,12 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config(a, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                             "l2": "no flush: per-step working set (merge table "
-                                   f"{infos[-1]['n_sigma'] * 32 / 1e9:.1f}+ GB) exceeds the 129 MB L2"}),
+        "config": config(a, world),
         "lanczos_steps_per_s": steps_per_s,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),
+        "workloads": workloads,
+        "pipe_rates": issue,
         "precision": precision,
         "heat_bath_screen": screen,
         "detail": {"n_in": infos[-1]["n_in"], "n_sigma": infos[-1]["n_sigma"],

@@ -181,14 +181,13 @@ sfci_status sfci_truncate_topk_noalloc(const uint64_t *rank, const double *coef,
 /* ---------------------------------------------------------- SFCI Lanczos */
 
 /* sfci_params.flags */
-/* Automatic bucket size (bucket_elems = 0) takes 2048-element merge buckets
- * into the 2048-slot tables on every sigma, not only once the previous
- * sigma's entries repeated 1.5 times on average.  A table that cannot hold a
- * bucket's distinct entries then makes the step redo that sigma with
- * 1024-element buckets (info->bucket_redo), with the same result.  Slower on
- * workloads whose entries are mostly distinct; it exists to exercise that
- * fallback. */
-#define SFCI_LZ_BIG_BUCKETS_ALWAYS 1u
+/* A test setting for the automatic bucket size (bucket_elems = 0): every
+ * sigma first tries 2048-element merge buckets in 1024-slot tables, which
+ * cannot hold a bucket with more than 1024 distinct entries; such a sigma is
+ * redone with the normal 1024-element buckets (info->bucket_redo), with the
+ * same result.  Exercises the fallback that a crowded 2048-element bucket
+ * takes in normal runs; slower. */
+#define SFCI_LZ_FALLBACK_STRESS 1u
 
 typedef struct sfci_params {
     int64_t n_keep;         /* N_d: entries kept per basis vector (Eq. 11)          */
@@ -197,7 +196,7 @@ typedef struct sfci_params {
     double conv_tol;        /* halt when E(n-1) - E(n) < conv_tol (Sec. 2.1); <= 0 off */
     int32_t n_lanczos;      /* N_L: basis vectors per cycle, w_0 included (Sec. 2.1) */
     int32_t max_iter;       /* the step that reaches this sigma count ends its cycle; <= 0 off */
-    uint32_t flags;         /* 0 or SFCI_LZ_BIG_BUCKETS_ALWAYS                        */
+    uint32_t flags;         /* 0 or SFCI_LZ_FALLBACK_STRESS                           */
     int32_t bucket_elems;   /* intermediate elements per merge bucket; 0 = automatic:
                                1024, or 2048 once the previous sigma had at least
                                1.5 elements per distinct entry (a table overflow
@@ -257,6 +256,8 @@ typedef struct sfci_step_info {
                               element, stream and overflow buffers (GB)              */
     int64_t n_overflow;    /* most elements any pass sent past their bucket's region  */
     double ms_alloc;       /* of ms_plan: device buffer (re)allocation               */
+    int64_t n_emitted;     /* intermediate elements generated for sigma_i and merged:
+                              the non-zero products of n_elements                */
 } sfci_step_info;
 
 typedef struct sfci_lanczos sfci_lanczos; /* opaque; owns w_0..w_{N_L-1}, T, S, table */
@@ -371,6 +372,19 @@ sfci_status sfci_rdm_energy(int n_orb, const double *rdm1, const double *rdm2, d
 sfci_status sfci_debug_excitations(const sfci_system *sys, const uint64_t *rank, int64_t n,
                                    int64_t *src, uint64_t *tgt, double *elem, int64_t cap,
                                    int64_t *n_out, void *stream);
+
+/* Diagnostic: the rate (lane operations per second) of one SM pipe operation
+ * that bounds the sigma kernels, measured alone on the current device with
+ * enough independent work per thread to fill the pipe.  kind: 0 float64
+ * fused multiply-add, 1 float64 add, 2 float64 multiply, 3 float32 fused
+ * multiply-add, 4 64-bit integer multiply-add, 5 64-bit integer atomic add on
+ * shared memory, 6 32-bit integer atomic add on shared memory, 7 64-bit
+ * compare-and-swap on shared memory.  iters in [1, 2^30] loop trips per
+ * thread (8 operations each for kinds 0-4, 2 for 5-7); workspace: 8 bytes of
+ * device memory.  Not part of the method: it gives the issue-rate ceilings
+ * against which the kernels' counters are read.  Synchronises the stream. */
+sfci_status sfci_debug_pipe_rate(int kind, int64_t iters, void *workspace, double *ops_per_s,
+                                 void *stream);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsfci.so")
 SFCI_OK, SFCI_E_INVALID, SFCI_E_CAPACITY, SFCI_E_OVERFLOW = 0, 1, 2, 3
 SFCI_E_CUDA, SFCI_E_TIMEOUT, SFCI_E_NOMEM = 4, 5, 6
 SFCI_FP32_ELEMENTS = 1  # sfci_system_create flag: float32 off-diagonal elements
-SFCI_LZ_BIG_BUCKETS_ALWAYS = 1  # sfci_params flag: 2048-element buckets on every sigma
+SFCI_LZ_FALLBACK_STRESS = 1  # sfci_params flag (tests): 2048-element buckets in 1024-slot tables
 
 
 class SfciError(RuntimeError):
@@ -52,7 +52,7 @@ class StepInfo(C.Structure):
                 ("n_passes", C.c_int32), ("n_buckets_log2", C.c_int32),
                 ("tau", C.c_double), ("cut", C.c_double), ("redo", C.c_int32), ("bucket_redo", C.c_int32),
                 ("pass_budget_gb", C.c_double), ("regions_gb", C.c_double), ("free_gb", C.c_double),
-                ("n_overflow", C.c_int64), ("ms_alloc", C.c_double)]
+                ("n_overflow", C.c_int64), ("ms_alloc", C.c_double), ("n_emitted", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -100,6 +100,7 @@ def lib():
         "sfci_rdm12": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp, C.POINTER(_f64), _vp, C.c_size_t, _vp]),
         "sfci_rdm_energy": (_i32, [_i32, _vp, _vp, _f64, _vp, _vp, _f64, C.POINTER(_f64), _vp, C.c_size_t,
                                    _vp]),
+        "sfci_debug_pipe_rate": (_i32, [_i32, _i64, _vp, C.POINTER(_f64), _vp]),
         "sfci_debug_excitations": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, C.POINTER(_i64), _vp]),
         "sfci_scan_create": (_i32, [C.POINTER(_vp), _i32, C.POINTER(_vp), C.POINTER(Params),
                                     C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_i64), _i32]),
@@ -449,6 +450,21 @@ class Scan:
             self.close()
         except Exception:
             pass
+
+
+PIPE_KINDS = ("fp64_fma", "fp64_add", "fp64_mul", "fp32_fma", "int64_mad", "smem_atomic_add_u64",
+              "smem_atomic_add_u32", "smem_cas_u64")
+
+
+def pipe_rate(kind, iters=1 << 14, stream=None):
+    """Lane operations per second of one pipe operation (sfci_debug_pipe_rate);
+    kind: an index or a name of PIPE_KINDS."""
+    k = PIPE_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    ws = torch.zeros(1, dtype=torch.int64, device="cuda")
+    out = C.c_double()
+    _check(lib().sfci_debug_pipe_rate(k, int(iters), _ptr(ws), C.byref(out), _stream(stream)),
+           "sfci_debug_pipe_rate")
+    return float(out.value)
 
 
 def kernel_launches():

@@ -497,6 +497,7 @@ struct MergeArgs {
     double *sumsq;                      // sum of u^2 over the non-zero entries off w_i, w_{i-1}
     unsigned long long *n_live;         // entries that survive the screen
     unsigned long long *n_nonzero;      // non-zero entries off w_i, w_{i-1} (streamed or not)
+    unsigned long long *n_read;         // intermediate elements merged (null: not counted)
     unsigned *queue;
     int *status;                        // bit 2: a bucket has too many distinct keys; bit 3: output full;
                                         // bit 5: an element outside the 2^-S fixed-point range

@@ -206,6 +206,8 @@ struct sfci_lanczos {
     unsigned long long *nnz = nullptr;  // device word: non-zero entries off w_i, w_{i-1}
     unsigned long long *tau_w = nullptr, *mark_w = nullptr;  // stream threshold bits, raise mark
     int *lock_w = nullptr;
+    unsigned long long *nread_w = nullptr;  // device word: intermediate elements merged
+    long long n_emitted = 0;            // of the last sigma (host copy)
     double *dmin = nullptr;             // device word: min |kept|
     int n_passes = 0, nb_log2 = 0;
 };
@@ -328,10 +330,11 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     // bucket (a bucket that still holds more distinct keys than slots is
     // reported by the merge, and sigma is redone with 1024)
     const double tau_entry = *tau_io;
-    const bool force_big = (z->p.flags & SFCI_LZ_BIG_BUCKETS_ALWAYS) != 0;
+    const bool force_big = (z->p.flags & SFCI_LZ_FALLBACK_STRESS) != 0;
     const bool big_auto = z->p.bucket_elems <= 0 && !z->small_buckets && (force_big || z->mult_prev >= z->big_thresh);
     const double per_bucket = z->p.bucket_elems > 0 ? (double)z->p.bucket_elems : (big_auto ? 2048.0 : 1024.0);
-    const int slots = big_auto ? 2048 : (per_bucket <= 1024.0 ? 2048 : (per_bucket <= 2048.0 ? 4096 : 8192));
+    const int slots = big_auto ? (force_big ? 1024 : 2048)
+                               : (per_bucket <= 1024.0 ? 2048 : (per_bucket <= 2048.0 ? 4096 : 8192));
     const bool row_mode = d.ca <= kMaxRows;
     const auto t_plan0 = std::chrono::steady_clock::now();
     sfci_status r;
@@ -697,6 +700,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             A.sumsq = z->msumsq;
             A.n_live = z->mlive;
             A.n_nonzero = z->nnz;
+            A.n_read = z->nread_w;
             A.queue = z->queue;
             A.status = z->mstatus;
             // in the automatic 2048-element mode a crowded table gives up early
@@ -724,14 +728,16 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         SFCI_CUDA(cudaMemcpyAsync(&hl, z->mlive, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaMemcpyAsync(&hz, z->nnz, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaMemcpyAsync(&hq, z->msumsq, 8, cudaMemcpyDeviceToHost, z->st));
-        unsigned long long tb = 0;
+        unsigned long long tb = 0, hr = 0;
         SFCI_CUDA(cudaMemcpyAsync(&tb, z->tau_w, 8, cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(&hr, z->nread_w, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaStreamSynchronize(z->st));
         std::memcpy(&tau, &tb, 8);  // as raised during the merge
         *tau_io = tau;
         if (hs == 0 && !ovf_short) {
             *n_out = ho, *n_live = hl, *n_nonzero = hz, *sumsq = hq;
             z->mult_prev = E / std::max(1.0, (double)hl);  // intermediate elements per sigma entry
+            z->n_emitted = (long long)hr;
             z->stream_prev = ho;
             z->ovf_used = (long long)max_ovf;
             if ((int)z->ovf_at.size() <= i) z->ovf_at.resize(i + 1, 0);
@@ -836,7 +842,7 @@ sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
     }
     if (params->emit_warps < 0 || params->emit_warps > 8 || params->mem_budget < 0 ||
         params->bucket_elems < 0 || !(params->eps_element >= 0.0) ||
-        (params->flags & ~SFCI_LZ_BIG_BUCKETS_ALWAYS) != 0) {
+        (params->flags & ~SFCI_LZ_FALLBACK_STRESS) != 0) {
         set_error("need 0 <= emit_warps <= 8, mem_budget, bucket_elems, eps_element >= 0, known flags");
         return SFCI_E_INVALID;
     }
@@ -884,6 +890,7 @@ sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
         z->tau_w = reinterpret_cast<unsigned long long *>(w + 64);
         z->mark_w = reinterpret_cast<unsigned long long *>(w + 72);
         z->lock_w = reinterpret_cast<int *>(w + 80);
+        z->nread_w = reinterpret_cast<unsigned long long *>(w + 88);
     }
     if (e != cudaSuccess) {
         destroy_lz(z);
@@ -966,6 +973,7 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
         info->n_elements = n_in * (d.n_conn + 1);
         info->n_sigma = (long long)n_live;
         info->bucket_redo = z->bucket_redo;
+        info->n_emitted = z->n_emitted;
         z->m_prev = (long long)n_live;
         z->nin_prev = n_in;
 

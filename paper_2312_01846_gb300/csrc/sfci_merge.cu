@@ -296,7 +296,7 @@ merge_kernel(MergeArgs A) {
     bool range_ok = true;
     if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u), s_tau = *(volatile unsigned long long *)A.tau_bits;
     double sq = 0.0;
-    unsigned long long n_live = 0, n_nonzero = 0;
+    unsigned long long n_live = 0, n_nonzero = 0, n_read = 0;
     __syncthreads();
     for (;;) {
         const unsigned bi = cur;  // bucket index within the pass
@@ -313,6 +313,7 @@ merge_kernel(MergeArgs A) {
         const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(A.elem) + (r0 - A.bk.boff[A.lo]);
         const ulonglong2 *ovs = reinterpret_cast<const ulonglong2 *>(A.ovf_sorted) + o0;
         const unsigned total = n_main + (unsigned)(o1 - o0);
+        n_read += tid == 0 ? total : 0u;
         // keys repeat a lot in a bucket past its region or holding more
         // elements than table slots: lanes sharing a key are summed first
         const bool hot = o1 > o0 || total > (unsigned)kSlots;
@@ -484,6 +485,7 @@ merge_kernel(MergeArgs A) {
         atomicAdd(A.n_live, n_live);
         atomicAdd(A.n_nonzero, n_nonzero);
     }
+    if (tid == 0 && A.n_read) atomicAdd(A.n_read, n_read);
     if (!range_ok) atomicOr(A.status, 32);
 }
 
@@ -700,6 +702,7 @@ cudaError_t launch_merge_t(const MergeArgs &A, cudaStream_t st) {
 cudaError_t launch_merge(const MergeArgs &A, int slots, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(A.queue, 0, 4, st);
     if (e != cudaSuccess) return e;
+    if (slots <= 1024) return launch_merge_t<1024>(A, st);
     if (slots <= 2048) return launch_merge_t<2048>(A, st);
     if (slots <= 4096) return launch_merge_t<4096>(A, st);
     return launch_merge_t<8192>(A, st);

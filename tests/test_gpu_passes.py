@@ -84,17 +84,18 @@ def test_overflow_limit_too_small_is_reported(sf):
 
 
 def test_big_bucket_fallback_is_exact(sf):
-    """Automatic bucket size forced to 2048 elements per 2048-slot table on
-    every sigma (SFCI_LZ_BIG_BUCKETS_ALWAYS).  From the aufbau determinant
-    sigma's entries are all distinct, so some tables cannot hold their
-    bucket's keys: those sigmas are redone with 1024-element buckets
-    (info["bucket_redo"]).  The run must equal, bit for bit, a run with
-    1024-element buckets throughout (exact sums, exact top-N_d)."""
+    """The automatic bucket size's fallback, forced: with
+    SFCI_LZ_FALLBACK_STRESS every sigma first tries 2048-element buckets in
+    1024-slot tables.  From the aufbau determinant most of sigma's entries are
+    distinct, so buckets with more than 1024 of them do not fit and those
+    sigmas are redone with 1024-element buckets (info["bucket_redo"]).  The
+    run must equal, bit for bit, a run with 1024-element buckets throughout
+    (exact sums, exact top-N_d)."""
     d = gen.config_system(2)
     gsys = sf.System.from_dict(d)
     n_keep, steps = 20_000, 12
     ref, r1, c1 = _run(sf, gsys, n_keep, steps, bucket_elems=1024)
-    big, r2, c2 = _run(sf, gsys, n_keep, steps, flags=sf.SFCI_LZ_BIG_BUCKETS_ALWAYS)
+    big, r2, c2 = _run(sf, gsys, n_keep, steps, flags=sf.SFCI_LZ_FALLBACK_STRESS)
     redo = [i["bucket_redo"] for i in big]
     print("sigmas redone with 1024-element buckets per step:", redo)
     assert sum(redo) >= 1
