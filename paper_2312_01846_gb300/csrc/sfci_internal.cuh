@@ -493,7 +493,6 @@ struct MergeArgs {
     int *lock;
     long long nkeep;
     int fix_shift;                      // S: sigma entries are summed exactly in units of 2^-S
-    int max_probe;                      // linear-probe bound of the table (beyond it: status bit 2)
     double *sumsq;                      // sum of u^2 over the non-zero entries off w_i, w_{i-1}
     unsigned long long *n_live;         // entries that survive the screen
     unsigned long long *n_nonzero;      // non-zero entries off w_i, w_{i-1} (streamed or not)

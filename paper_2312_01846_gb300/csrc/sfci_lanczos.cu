@@ -703,10 +703,6 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
             A.n_read = z->nread_w;
             A.queue = z->queue;
             A.status = z->mstatus;
-            // in the automatic 2048-element mode a crowded table gives up early
-            // (the sigma is redone with 1024-element buckets); otherwise the
-            // probe runs until it finds the key or a free slot
-            A.max_probe = big_auto ? 512 : slots;
             SFCI_CUDA(launch_merge(A, slots, z->st));
             SFCI_CUDA(cudaEventRecord(z->evp[2], z->st));
             unsigned long long ovf_here = 0;

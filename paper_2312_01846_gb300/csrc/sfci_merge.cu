@@ -286,17 +286,17 @@ merge_kernel(MergeArgs A) {
     __shared__ unsigned cur, n_occ;
     __shared__ unsigned long long s_tau;
     __shared__ int s_raise, s_bin;
+    __shared__ unsigned long long s_nread;  // elements merged by this CTA (kept out of registers)
     const int tid = threadIdx.x, lane = tid & 31;
     const bool screen = A.eps > 0.0;
     // thresholds compared on bit patterns (|x| < t for t >= 0, NaN never below)
     const unsigned long long eps_bits = abs_bits(A.eps);
     for (int sl = tid; sl < kSlots; sl += kMT) keys[sl] = kEmpty, acc_lo[sl] = 0ull, acc_hi[sl] = 0ull, flag[sl] = 0;
     const int S = A.fix_shift;
-    const int max_probe = A.max_probe > 0 && A.max_probe < kSlots ? A.max_probe : kSlots;
     bool range_ok = true;
-    if (tid == 0) n_occ = 0, cur = atomicAdd(A.queue, 1u), s_tau = *(volatile unsigned long long *)A.tau_bits;
+    if (tid == 0) n_occ = 0, s_nread = 0, cur = atomicAdd(A.queue, 1u), s_tau = *(volatile unsigned long long *)A.tau_bits;
     double sq = 0.0;
-    unsigned long long n_live = 0, n_nonzero = 0, n_read = 0;
+    unsigned long long n_live = 0, n_nonzero = 0;
     __syncthreads();
     for (;;) {
         const unsigned bi = cur;  // bucket index within the pass
@@ -313,7 +313,7 @@ merge_kernel(MergeArgs A) {
         const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(A.elem) + (r0 - A.bk.boff[A.lo]);
         const ulonglong2 *ovs = reinterpret_cast<const ulonglong2 *>(A.ovf_sorted) + o0;
         const unsigned total = n_main + (unsigned)(o1 - o0);
-        n_read += tid == 0 ? total : 0u;
+        if (tid == 0) s_nread += total;
         // keys repeat a lot in a bucket past its region or holding more
         // elements than table slots: lanes sharing a key are summed first
         const bool hot = o1 > o0 || total > (unsigned)kSlots;
@@ -356,7 +356,7 @@ merge_kernel(MergeArgs A) {
                 bool ins = false, found = false;
                 if (act) {
                     h = smem_slot<kSlots>(key, A.bk.rowmap ? 0 : A.bk.log2B);
-                    for (int probe = 0; probe < max_probe; ++probe) {
+                    for (int probe = 0; probe < kSlots; ++probe) {
                         const unsigned long long c = keys[h];
                         if (c == key) {
                             found = true;
@@ -384,8 +384,22 @@ merge_kernel(MergeArgs A) {
                 }
                 if (act) {
                     if (found) {
-                        const unsigned long long old = atomicAdd(&acc_lo[h], f.lo);
-                        atomicAdd(&acc_hi[h], f.hi + (old + f.lo < old ? 1ull : 0ull));  // with the carry
+                        // the 128-bit sum as four 32-bit limbs, each added with a native
+                        // 32-bit shared-memory atomic and the carry passed up by hand
+                        // (64-bit shared atomics run at a sixth of the 32-bit rate)
+                        unsigned *l32 = reinterpret_cast<unsigned *>(acc_lo) + 2 * h;
+                        unsigned *h32 = reinterpret_cast<unsigned *>(acc_hi) + 2 * h;
+                        const unsigned w0 = (unsigned)f.lo, w1 = (unsigned)(f.lo >> 32);
+                        const unsigned w2 = (unsigned)f.hi, w3 = (unsigned)(f.hi >> 32);
+                        unsigned o = atomicAdd(l32, w0);
+                        unsigned c = (o + w0) < o;
+                        unsigned x = w1 + c, cx = c & (w1 == 0xFFFFFFFFu);  // w1 + c wrapped: carry out
+                        o = atomicAdd(l32 + 1, x);
+                        c = cx | ((o + x) < o);
+                        x = w2 + c, cx = c & (w2 == 0xFFFFFFFFu);
+                        o = atomicAdd(h32, x);
+                        c = cx | ((o + x) < o);
+                        atomicAdd(h32 + 1, w3 + c);
                     } else {
                         atomicOr(A.status, 4);
                     }
@@ -485,7 +499,7 @@ merge_kernel(MergeArgs A) {
         atomicAdd(A.n_live, n_live);
         atomicAdd(A.n_nonzero, n_nonzero);
     }
-    if (tid == 0 && A.n_read) atomicAdd(A.n_read, n_read);
+    if (tid == 0 && A.n_read) atomicAdd(A.n_read, s_nread);
     if (!range_ok) atomicOr(A.status, 32);
 }
 
