@@ -59,7 +59,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-workloads", action="store_true",
                    help="skip the rows of the other workloads (8-orbital full space, Hubbard ring, "
-                        "N_d = 1e5, RDM pass) and the pipe-rate probes")
+                        "N_d = 1e5, RDM pass, batched scan) and the pipe-rate probes")
     p.add_argument("--bucket-elems", type=int, default=0,
                    help="intermediate elements per merge bucket (0 = automatic)")
     p.add_argument("--table-capacity", type=int, default=0,
@@ -279,51 +279,96 @@ def precision_study(sf, d, nkeep, n_lanczos, steps, stream):
     return out
 
 
-def run_scan(a):
-    """Batched scan: the 32 uneven instances (n 16-24, 5-8 electrons per spin,
-    caps 1e4-2e5, integrals interpolated between two seeded sets) stepped
-    together through sfci_scan, and the same instances one at a time (one
-    worker) for comparison.  value = intermediate elements of all instances
-    per second of wall time (each scan step returns when every instance's step
-    is done on the device)."""
+def scan_study(sf, cap_scale, n_lanczos, warmup, steps, workers=0, bucket_elems=0, emit_warps=0):
+    """The 32-instance batched scan (n 16-24, 5-8 electrons per spin, caps
+    1e4-2e5 times cap_scale, integrals interpolated between two seeded sets)
+    stepped together through sfci_scan (float64, then float32 elements), and
+    the float64 instances one at a time (one worker) for comparison.  Per run:
+    elements of all instances per second of wall time, and the device-busy
+    fraction sum over instances of (sigma + truncation time, CUDA events) / wall
+    time; the float32 run's energy difference from the float64 run at every
+    cycle end, per instance."""
     import numpy as np
     import torch
 
     import gen
+    inst_d = gen.batched_scan_instances()
+    caps = [max(1000, int(d["cap"] * cap_scale)) for d in inst_d]
+    out = {"workload": f"batched-scan-32-instances-n16to24-caps1e4to2e5x{cap_scale:g}", "caps": caps,
+           "n_lanczos": n_lanczos, "warmup": warmup, "steps": steps}
+    lams = {}
+    for name, workers_, flags in (("batched", workers, 0), ("one_at_a_time", 1, 0),
+                                  ("batched_fp32_elements", workers, sf.SFCI_FP32_ELEMENTS)):
+        systems = [sf.System.from_dict(d, flags=flags) for d in inst_d]
+        inst = [(s_, np.array([0], dtype=np.uint64), np.array([1.0]), c) for s_, c in zip(systems, caps)]
+        sc = sf.Scan(inst, n_lanczos=n_lanczos, bucket_elems=bucket_elems, emit_warps=emit_warps,
+                     workers=workers_)
+        allsteps = [sc.step() for _ in range(warmup)]
+        torch.cuda.synchronize()
+        l0 = sf.kernel_launches()
+        t0 = time.perf_counter()
+        timed = [sc.step() for _ in range(steps)]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        allsteps += timed
+        el = sum(x["n_elements"] for st in timed for x in st)
+        busy = sum(x["ms_sigma"] + x["ms_topk"] for st in timed for x in st) * 1e-3
+        out[name] = {"value": el / dt, "ms_per_step": 1e3 * dt / steps, "elements_per_step": el / steps,
+                     "gpu_launches": sf.kernel_launches() - l0, "device_busy_fraction": busy / dt}
+        lams[name] = [[st[k]["lambda_min"] for st in allsteps if st[k]["cycle_end"]] for k in range(len(caps))]
+        if name == "batched":
+            final = [sc.vector(k) for k in range(len(caps))]
+        sc.close()
+        for s_ in systems:
+            s_.close()
+    out["speedup_vs_one_at_a_time"] = out["batched"]["value"] / out["one_at_a_time"]["value"]
+    out["fp32_speedup"] = out["batched_fp32_elements"]["value"] / out["batched"]["value"]
+    d64, d32 = lams["batched"], lams["batched_fp32_elements"]
+    out["fp32_delta_e_hartree"] = [[b - a for a, b in zip(x, y)] for x, y in zip(d64, d32)]  # per instance
+    out["fp32_max_abs_delta_e"] = max((abs(v) for row in out["fp32_delta_e_hartree"] for v in row), default=None)
+    out["lambda_cycle_ends_fp64"] = d64
+    # element precision alone: <psi|H|psi> / <psi|psi> of the float64 run's final
+    # vector of each instance, with float64 and with float32 elements (one step of
+    # a one-vector solver gives a_0 = the Rayleigh quotient)
+    same = []
+    for k, d in enumerate(inst_d):
+        r, c = final[k]
+        a_ = []
+        for flags in (0, sf.SFCI_FP32_ELEMENTS):
+            s_ = sf.System.from_dict(d, flags=flags)
+            lz = sf.Lanczos(s_, r, c, caps[k], 1)
+            a_.append(lz.step()["a"])
+            lz.close()
+            s_.close()
+        same.append(a_[1] - a_[0])
+    out["fp32_delta_e_same_vector_hartree"] = same
+    out["fp32_max_abs_delta_e_same_vector"] = max(abs(x) for x in same)
+    out["fp32_within_1_uHa_same_vector"] = bool(max(abs(x) for x in same) <= 1e-6)
+    return out
+
+
+def run_scan(a):
+    """--workload scan: the batched scan as the JSON line's headline (see scan_study)."""
+    import torch
+
     import paper_2312_01846_gb300 as sf
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    inst_d = gen.batched_scan_instances()
-    systems = [sf.System.from_dict(d) for d in inst_d]
-    caps = [max(1000, int(d["cap"] * a.scan_cap_scale)) for d in inst_d]
     shape = {"bucket_elems": a.bucket_elems, "emit_warps": a.emit_warps, "workers": a.workers}
     tuned = None
     if a.tune:
+        import gen
         from paper_2312_01846_gb300.tune import tune_scan
-        tcaps = [max(1000, int(c * a.tune_cap_scale)) for c in caps]
+        inst_d = gen.batched_scan_instances()
+        systems = [sf.System.from_dict(d) for d in inst_d]
+        tcaps = [max(1000, int(d["cap"] * a.scan_cap_scale * a.tune_cap_scale)) for d in inst_d]
         tuned = tune_scan(systems, tcaps, n_lanczos=a.nlanczos)
         shape.update(tuned["best"])
-    out = {}
-    for name, workers in (("batched", shape["workers"]), ("one_at_a_time", 1)):
-        inst = [(s_, np.array([0], dtype=np.uint64), np.array([1.0]), c) for s_, c in zip(systems, caps)]
-        sc = sf.Scan(inst, n_lanczos=a.nlanczos, bucket_elems=shape["bucket_elems"],
-                     emit_warps=shape["emit_warps"], workers=workers)
-        for _ in range(a.warmup):
-            sc.step()
-        torch.cuda.synchronize()
-        l0 = sf.kernel_launches()
-        t0 = time.perf_counter()
-        steps = [sc.step() for _ in range(a.steps)]
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        el = sum(x["n_elements"] for st in steps for x in st)
-        out[name] = {"value": el / dt, "ms_per_step": 1e3 * dt / a.steps, "elements_per_step": el / a.steps,
-                     "gpu_launches": sf.kernel_launches() - l0,
-                     "lambda_last": [x["lambda_min"] for x in steps[-1]] if steps else None}
-        sc.close()
-        if rank != 0:
-            break
+        for s_ in systems:
+            s_.close()
+    out = scan_study(sf, a.scan_cap_scale, a.nlanczos, a.warmup, a.steps, shape["workers"],
+                     shape["bucket_elems"], shape["emit_warps"])
     hbm, peak_kind = peaks()
     b = out["batched"]
     achieved = BYTES_PER_ELEMENT * b["elements_per_step"] / (b["ms_per_step"] * 1e-3) / 1e9
@@ -331,22 +376,17 @@ def run_scan(a):
         "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"batched-scan-32-instances-n16to24-caps1e4to2e5x{a.scan_cap_scale:g}",
-                   "instances": len(systems), "caps": caps, "n_lanczos": a.nlanczos,
-                   "parallelism": "single GPU, one stream per instance"},
+        "config": {"workload": out["workload"], "instances": len(out["caps"]), "caps": out["caps"],
+                   "n_lanczos": a.nlanczos, "parallelism": "single GPU, one stream per instance"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "kernel": "whole scan step (wall time)",
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "model": f"{BYTES_PER_ELEMENT} B per connected element"},
         "gpu_launches": b["gpu_launches"], "cpu_baseline": None, "e2e": None,
-        "detail": out, "speedup_vs_one_at_a_time": (b["value"] / out["one_at_a_time"]["value"]
-                                                    if "one_at_a_time" in out else None),
-        "launch_shape": shape, "autotune": tuned,
+        "detail": out, "launch_shape": shape, "autotune": tuned,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for s_ in systems:
-        s_.close()
     return 0
 
 
@@ -554,9 +594,10 @@ def run_ours(a):
                 "sigma_share_of_step": sum(i["ms_sigma"] for i in infos) / ms}
 
     # end to end through the public API with host buffers, chained: each step
-    # copies its input vector host -> device, restarts the solver from it
-    # (sfci_lanczos_load), runs one step, and copies the next basis vector back
-    # to the host, where it is the next step's input
+    # copies its input vector w_i host -> device and hands it to the solver
+    # (sfci_lanczos_set_input, the cycle goes on), runs one step, and copies
+    # the next vector (w_{i+1}, or the restart vector) back to the host, where
+    # it is the next step's input
     e2e = None
     if not a.no_e2e:
         r_dev, c_dev = lz.vector()
@@ -566,7 +607,7 @@ def run_ours(a):
         h_r[: r_dev.numel()].copy_(r_dev)
         h_c[: c_dev.numel()].copy_(c_dev)
         n_cur = r_dev.numel()
-        n_e2e = max(1, min(a.steps, 5))
+        n_e2e = max(1, min(a.steps, 10))
         barrier()
         t0 = time.perf_counter()
         el2 = 0
@@ -574,7 +615,7 @@ def run_ours(a):
         for _ in range(n_e2e):
             dr = h_r[:n_cur].to("cuda", non_blocking=True)
             dc = h_c[:n_cur].to("cuda", non_blocking=True)
-            lz.load(dr, dc)
+            lz.set_input(dr, dc)
             info = lz.step()
             el2 += info["n_elements"]
             nr, nc = lz.vector()
@@ -588,8 +629,8 @@ def run_ours(a):
         dt = time.perf_counter() - t0
         e2e = {"value": el2 / dt, "unit": UNIT, "h2d_bytes_per_step": h2d // n_e2e,
                "d2h_bytes_per_step": d2h // n_e2e, "steps": n_e2e,
-               "note": "chained: host vector in, restart + one step, next vector to the host as the "
-                       "next step's input (wall clock)"}
+               "note": "chained: host vector in (set as the solver's w_i), one step, the next vector "
+                       "to the host as the next step's input (wall clock)"}
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
@@ -618,6 +659,7 @@ def run_ours(a):
             "cfg2_nd1e5": solver_row(sf, d, "sfci-28o-7a7b-L200-clustered-Nd1e5-NL10", 100_000, 10, 4, 16,
                                      stream, "same system as the headline at N_d = 1e5"),
             "cfg4_rdm": rdm_row(sf, stream),
+            "cfg3_scan": scan_study(sf, 1.0, a.nlanczos, 3, 8),
         }
     issue = pipe_rates(sf) if rank == 0 and not a.no_workloads else None
 

@@ -280,7 +280,12 @@ sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
  * that the N_d-th kept |u| is >= tau; if not, it recomputes sigma with the
  * exact threshold read off a magnitude histogram of this attempt (info->redo),
  * so the kept set is the exact top-N_d of Eq. 11 either way.
- * SFCI_E_CAPACITY only if sigma's buffers cannot grow in device memory. */
+ * SFCI_E_CAPACITY only if sigma's buffers cannot grow in device memory.
+ * Observability: when the environment variable SFCI_STEP_LOG names a file,
+ * every step appends one JSON line to it (iteration, cycle, lambda, a, b,
+ * ||u||, entries kept, elements, stage times and the sigma stage's rate
+ * under 32 bytes per element); the stages are also marked as NVTX ranges
+ * for a profiler's timeline. */
 sfci_status sfci_lanczos_step(sfci_lanczos *lz, sfci_step_info *info);
 /* Restart the solver from a new trial vector (device pointers, ranks strictly
  * ascending): it is truncated to n_keep and normalised into w_0, and a new
@@ -288,6 +293,15 @@ sfci_status sfci_lanczos_step(sfci_lanczos *lz, sfci_step_info *info);
  * stream vectors through the solver without re-creating it. */
 sfci_status sfci_lanczos_load(sfci_lanczos *lz, const uint64_t *rank, const double *coef,
                               int64_t n);
+/* Overwrite the current input vector (the w_i the next step will use) with a
+ * caller's copy, keeping the cycle's T, S and w_0 .. w_{i-1}: resuming a run
+ * whose vectors live elsewhere (a host checkpoint, another process).  The
+ * vector (device pointers, ranks strictly ascending, 1 <= n <= n_keep) is
+ * taken as it is: it should be the w_i that sfci_lanczos_vector returned,
+ * or the cycle's T and S no longer describe the basis.  SFCI_E_CAPACITY if
+ * n > n_keep.  Synchronises the solver's stream. */
+sfci_status sfci_lanczos_set_input(sfci_lanczos *lz, const uint64_t *rank, const double *coef,
+                                   int64_t n);
 /* Copy the current input vector (the w_i the next step will use) to device
  * buffers with room for cap entries; *n (host) = its length. */
 sfci_status sfci_lanczos_vector(const sfci_lanczos *lz, uint64_t *rank, double *coef,

@@ -77,6 +77,7 @@ def lib():
         "sfci_version": (_i32, []),
         "sfci_kernel_launches": (_i64, []),
         "sfci_lanczos_load": (_i32, [_vp, _vp, _vp, _i64]),
+        "sfci_lanczos_set_input": (_i32, [_vp, _vp, _vp, _i64]),
         "sfci_system_create": (_i32, [C.POINTER(_vp), _i32, _i32, _i32, _vp, _vp, _f64, C.c_uint32]),
         "sfci_system_destroy": (_i32, [_vp]),
         "sfci_dim": (_i32, [_vp, C.POINTER(_u64)]),
@@ -370,6 +371,13 @@ class Lanczos:
         _check(lib().sfci_lanczos_load(self.handle, _ptr(r), _ptr(c), r.numel()),
                "sfci_lanczos_load")
 
+    def set_input(self, rank, coef):
+        """Replace the current input vector w_i, keeping the cycle (sfci_lanczos_set_input)."""
+        r = _dev(rank, torch.int64)
+        c = _dev(coef, torch.float64)
+        _check(lib().sfci_lanczos_set_input(self.handle, _ptr(r), _ptr(c), r.numel()),
+               "sfci_lanczos_set_input")
+
     def vector(self):
         cap = int(self.params.n_keep)
         r = torch.empty(cap, dtype=torch.int64, device="cuda")
@@ -439,6 +447,17 @@ class Scan:
         n = C.c_int64()
         _check(lib().sfci_lanczos_vector(z, _ptr(r), _ptr(c), cap, C.byref(n)), "sfci_lanczos_vector")
         return r[: n.value], c[: n.value]
+
+    def matrices(self, i):
+        """T and S of instance i (sfci_lanczos_matrices of its solver)."""
+        import numpy as np
+        z = C.c_void_p()
+        _check(lib().sfci_scan_solver(self.handle, int(i), C.byref(z)), "sfci_scan_solver")
+        NL = int(self.params[i].n_lanczos)
+        T = np.zeros((NL, NL))
+        S = np.zeros((NL, NL))
+        _check(lib().sfci_lanczos_matrices(z, T.ctypes.data, S.ctypes.data), "sfci_lanczos_matrices")
+        return T, S
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

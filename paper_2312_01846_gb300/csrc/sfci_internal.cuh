@@ -40,35 +40,38 @@ struct Fix128 {
     unsigned long long lo, hi;
 };
 
+// 64-bit shifts whose amount may be 64 or more (the PTX shift instructions
+// clamp the amount to the register width, so the result is 0)
+__device__ __forceinline__ unsigned long long shl64(unsigned long long x, unsigned s) {
+    unsigned long long r;
+    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
+}
+__device__ __forceinline__ unsigned long long shr64(unsigned long long x, unsigned s) {
+    unsigned long long r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
+}
+
+// Without branches (lanes holding elements of different magnitudes do not
+// diverge): both shift directions are formed and one is selected, and the
+// two's-complement negation is a masked xor plus a carried one.
 __device__ __forceinline__ Fix128 to_fixed(double v, int S, bool &range_ok) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-    unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
-    int ex = (int)((bits >> 52) & 0x7FF);
-    Fix128 x{0ull, 0ull};
-    if (ex == 0 && mant == 0) return x;
-    if (ex) mant |= 1ull << 52;
-    else ex = 1;
-    const int sh = ex - 1075 + S;  // v = mant 2^(ex-1075)
-    if (sh > 74) {                 // would not fit in 127 bits
-        range_ok = false;
-        return x;
-    }
-    if (sh >= 64) {
-        x.hi = mant << (sh - 64);
-    } else if (sh > 0) {
-        x.lo = mant << sh;
-        x.hi = mant >> (64 - sh);
-    } else if (sh == 0) {
-        x.lo = mant;
-    } else if (-sh <= 63) {
-        const int r = -sh;
-        x.lo = (mant >> r) + ((mant >> (r - 1)) & 1ull);  // nearest, ties away from zero
-    }
-    if (bits >> 63) {  // negate
-        x.lo = ~x.lo + 1ull;
-        x.hi = ~x.hi + (x.lo == 0ull ? 1ull : 0ull);
-    }
-    return x;
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (ex ? (1ull << 52) : 0ull);
+    const int sh = (ex ? ex : 1) - 1075 + S;  // v = mant 2^(ex-1075): mant 2^sh units
+    if (sh > 74 && mant) range_ok = false;      // would not fit in 127 bits
+    const unsigned su = (unsigned)sh, r = (unsigned)(-sh);
+    // sh >= 0: mant << sh as 128 bits; sh < 0: mant >> -sh, nearest, ties away from zero
+    const unsigned long long lo_p = shl64(mant, su), hi_p = shr64(mant, 64u - su) | shl64(mant, su - 64u);
+    const unsigned long long lo_n = shr64(mant, r) + (shr64(mant, r - 1u) & 1ull);
+    unsigned long long lo = sh >= 0 ? lo_p : lo_n, hi = sh >= 0 ? hi_p : 0ull;
+    const unsigned long long neg = (unsigned long long)((long long)bits >> 63);  // all ones if v < 0
+    lo ^= neg, hi ^= neg;
+    const unsigned long long one = neg & 1ull, lo2 = lo + one;
+    hi += one & (lo2 == 0ull ? 1ull : 0ull);
+    return Fix128{lo2, hi};
 }
 
 // the sum held in (lo, hi) as a double, rounded to nearest, ties to even

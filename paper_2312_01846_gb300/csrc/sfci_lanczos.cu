@@ -16,10 +16,15 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "sfci_internal.cuh"
 
@@ -134,6 +139,39 @@ double gen_eig_lowest(int m, const std::vector<double> &T, const std::vector<dou
         x[a] = acc;
     }
     return lam[0];
+}
+
+// NVTX range for the lifetime of a scope (a no-op unless a profiler attaches)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+// One JSON line per step appended to the file named by SFCI_STEP_LOG (when set):
+// the step's scalars, stage times and the sigma stage's rate.
+std::mutex g_log_mu;
+
+void log_step(const sfci_step_info &s) {
+    const char *path = std::getenv("SFCI_STEP_LOG");
+    if (!path || !*path) return;
+    std::lock_guard<std::mutex> lk(g_log_mu);
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    const double gbs = s.ms_sigma > 0.0 ? 32.0 * (double)s.n_elements / (s.ms_sigma * 1e-3) / 1e9 : 0.0;
+    std::fprintf(f,
+                 "{\"iter\": %d, \"cycle\": %d, \"index\": %d, \"cycle_end\": %d, \"converged\": %d, "
+                 "\"breakdown\": %d, \"lambda_min\": %.17g, \"a\": %.17g, \"b\": %.17g, \"u_norm\": %.17g, "
+                 "\"n_in\": %lld, \"n_sigma\": %lld, \"n_kept\": %lld, \"n_elements\": %lld, "
+                 "\"n_emitted\": %lld, \"n_psi\": %lld, \"ms_step\": %.4f, \"ms_sigma\": %.4f, "
+                 "\"ms_emit\": %.4f, \"ms_merge\": %.4f, \"ms_plan\": %.4f, \"ms_topk\": %.4f, "
+                 "\"n_passes\": %d, \"redo\": %d, \"bucket_redo\": %d, \"n_overflow\": %lld, "
+                 "\"sigma_gbs_32B_per_element\": %.3f}\n",
+                 s.iter, s.cycle, s.index, s.cycle_end, s.converged, s.breakdown, s.lambda_min, s.a, s.b,
+                 s.u_norm, (long long)s.n_in, (long long)s.n_sigma, (long long)s.n_kept,
+                 (long long)s.n_elements, (long long)s.n_emitted, (long long)s.n_psi, s.ms_step, s.ms_sigma,
+                 s.ms_emit, s.ms_merge, s.ms_plan, s.ms_topk, s.n_passes, s.redo, s.bucket_redo,
+                 (long long)s.n_overflow, gbs);
+    std::fclose(f);
 }
 
 }  // namespace
@@ -823,6 +861,27 @@ sfci_status sfci_lanczos_load(sfci_lanczos *z, const uint64_t *rank, const doubl
     return load_vector(z, rank, coef, n);
 }
 
+sfci_status sfci_lanczos_set_input(sfci_lanczos *z, const uint64_t *rank, const double *coef, int64_t n) {
+    if (!z || n < 0 || (n > 0 && (!rank || !coef))) {
+        set_error("need a solver and device vectors");
+        return SFCI_E_INVALID;
+    }
+    if (n > z->nkeep) {
+        set_error("the vector has more entries than n_keep");
+        return SFCI_E_CAPACITY;
+    }
+    if (n == 0) {
+        set_error("the input vector must not be empty");
+        return SFCI_E_INVALID;
+    }
+    const int i = z->idx;
+    SFCI_CUDA(cudaMemcpyAsync(z->wr[i], rank, size_t(n) * 8, cudaMemcpyDeviceToDevice, z->st));
+    SFCI_CUDA(cudaMemcpyAsync(z->wc[i], coef, size_t(n) * 8, cudaMemcpyDeviceToDevice, z->st));
+    SFCI_CUDA(cudaStreamSynchronize(z->st));
+    z->wn[i] = n;
+    return SFCI_OK;
+}
+
 sfci_status sfci_lanczos_create(sfci_lanczos **out, const sfci_system *sys,
                                 const sfci_params *params, const uint64_t *init_rank,
                                 const double *init_coef, int64_t n_init, void *stream) {
@@ -926,6 +985,7 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
         return SFCI_E_INVALID;
     }
     std::memset(info, 0, sizeof(*info));
+    NvtxRange nv_step("sfci_lanczos_step");
     const SysDev &d = z->sys->d;
     const int i = z->idx, NL = z->NL;
     z->bucket_redo = 0;
@@ -952,6 +1012,7 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
         unsigned long long n_stream = 0, n_live = 0, n_nz = 0;
         double sq = 0.0;
         {
+            NvtxRange nv("sigma (plan, emit, merge)");
             const sfci_status rs = bucketed_sigma(z, i, &tau, &n_stream, &n_live, &n_nz, &sq);
             if (rs != SFCI_OK) return rs;
         }
@@ -992,6 +1053,7 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
 
         // u = sigma_i - a w_i - b w_{i-1} on the support of w_i and w_{i-1} (Eq. 10);
         // elsewhere u = sigma_i, streamed where |u| >= tau
+        NvtxRange nv_trunc("u and truncation (Eq. 10-11)");
         SFCI_CUDA(cudaEventRecord(z->evp[3], z->st));
         const VecRef wi = vr[i];
         const VecRef wm = i > 0 ? vr[i - 1] : VecRef{nullptr, nullptr, 0};
@@ -1089,6 +1151,7 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
     info->index = i;
     info->n_in = n_in;
     if (last) {
+        NvtxRange nv_end("cycle end (eigensolve, restart)");
         const int m = i + 1;
         std::vector<double> Tm(size_t(m) * m), Sm(size_t(m) * m);
         for (int r = 0; r < m; ++r)
@@ -1133,6 +1196,7 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, z->ev[0], z->ev[3]);
     info->ms_step = ms;
+    log_step(*info);
     return SFCI_OK;
 }
 

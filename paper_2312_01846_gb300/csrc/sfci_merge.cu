@@ -330,8 +330,8 @@ merge_kernel(MergeArgs A) {
             for (int k = 0; k < kPre; ++k) {
                 if (e0 + (unsigned)k * kMT >= total) break;  // block-uniform: no elements left
                 const unsigned long long key = x[k].x;
-                Fix128 f{0ull, 0ull};
-                if (key != kEmpty) f = to_fixed(__longlong_as_double((long long)x[k].y), S, range_ok);
+                // (a place left empty holds the value 0, which converts to 0)
+                Fix128 f = to_fixed(__longlong_as_double((long long)x[k].y), S, range_ok);
                 bool act = key != kEmpty;
                 if (hot) {
                     // lanes holding the same key: the lowest one sums the group's

@@ -92,21 +92,26 @@ def _check_kept(gr, gc, ur, uv, tol, n_keep, orc, label, sign=1.0):
     return int(diff.size)
 
 
-def _replay(sf, orc, d, n_keep, n_lanczos, n_iter, label):
-    gsys, osys = sf.System.from_dict(d), orc.System.from_dict(d)
-    lz = sf.Lanczos(gsys, np.array([0], dtype=np.uint64), np.array([1.0]), n_keep, n_lanczos,
-                    max_iter=n_iter)
-    W = [_vec(sf, lz)]
-    T_or = np.zeros((n_lanczos, n_lanczos))
-    S_or = np.zeros((n_lanczos, n_lanczos))
-    n_diff, n_cycles, energies = 0, 0, []
-    for step in range(n_iter):
-        info = lz.step()
+class Replay:
+    """Oracle replay of one solver: feed it each step's info, the solver's T and
+    S after the step (sfci_lanczos_matrices) and its next input vector."""
+
+    def __init__(self, orc, osys, w0, n_keep, n_lanczos, label):
+        self.orc, self.osys, self.n_keep, self.label = orc, osys, n_keep, label
+        self.W = [w0]
+        self.T_or = np.zeros((n_lanczos, n_lanczos))
+        self.S_or = np.zeros((n_lanczos, n_lanczos))
+        self.n_diff = self.n_cycles = self.steps = 0
+        self.energies = []
+
+    def step(self, info, Tg, Sg, nxt):
+        orc, W, T_or, S_or, n_keep = self.orc, self.W, self.T_or, self.S_or, self.n_keep
+        label, step = self.label, self.steps
+        self.steps += 1
         i = info["index"]
         assert i == len(W) - 1
         wr, wc = W[i]
-        sr, sv, sa, _ = orc.sigma(osys, wr, wc)
-        Tg, Sg = lz.matrices()
+        sr, sv, sa, _ = orc.sigma(self.osys, wr, wc)
         for j in range(i + 1):
             rj, cj = W[j]
             t = float(np.dot(cj, _on(sr, sv, rj)))
@@ -130,10 +135,9 @@ def _replay(sf, orc, d, n_keep, n_lanczos, n_iter, label):
                 db = TOL * float(np.dot(np.abs(cm), _on(sr, sa, rm)))
                 wm_u = np.abs(_on(rm, cm, ur))
                 tol = tol + TOL * abs(b) * wm_u + db * wm_u
-            nxt = _vec(sf, lz)
-            n_diff += _check_kept(nxt[0], nxt[1], ur, uv, tol, n_keep, orc, f"{label} step {step}")
+            self.n_diff += _check_kept(nxt[0], nxt[1], ur, uv, tol, n_keep, orc, f"{label} step {step}")
             W.append(nxt)
-            continue
+            return
         # cycle end: the generalised eigenproblem of this cycle
         m = i + 1
         sym = lambda X: np.triu(X[:m, :m]) + np.triu(X[:m, :m], 1).T  # noqa: E731
@@ -141,7 +145,7 @@ def _replay(sf, orc, d, n_keep, n_lanczos, n_iter, label):
         lam_o, _ = orc.gen_eig_lowest(sym(T_or), sym(S_or))
         assert abs(info["lambda_min"] - lam_g) < 1e-9, (label, step, info["lambda_min"], lam_g)
         assert abs(info["lambda_min"] - lam_o) < 1e-9, (label, step, info["lambda_min"], lam_o)
-        energies.append(info["lambda_min"])
+        self.energies.append(info["lambda_min"])
         # restart vector: Psi = sum_j x_j w_j (ascending j), top N_d, normalised
         allr = np.unique(np.concatenate([w[0] for w in W]))
         acc = np.zeros(allr.size)
@@ -150,7 +154,6 @@ def _replay(sf, orc, d, n_keep, n_lanczos, n_iter, label):
             pos = np.searchsorted(allr, rj)
             acc[pos] = acc[pos] + x_g[j] * cj
             asum[pos] = asum[pos] + np.abs(x_g[j] * cj)
-        nxt = _vec(sf, lz)
         # the eigenvector's sign is free: match it on the largest entry
         big = np.argmax(np.abs(acc))
         g_big = _on(nxt[0], nxt[1], allr[big:big + 1])[0]
@@ -158,16 +161,27 @@ def _replay(sf, orc, d, n_keep, n_lanczos, n_iter, label):
         # x is known to the two eigensolvers' rounding (Jacobi on the GPU's host
         # side, LAPACK here): 1e-10 of each entry's terms and 1e-12 of the largest
         tol = 1e-10 * asum + 1e-12 * np.abs(acc).max()
-        n_diff += _check_kept(nxt[0], nxt[1], allr, acc, tol, n_keep, orc, f"{label} restart {step}", sign)
-        W = [nxt]
+        self.n_diff += _check_kept(nxt[0], nxt[1], allr, acc, tol, n_keep, orc, f"{label} restart {step}", sign)
+        self.W = [nxt]
         T_or[:] = 0.0
         S_or[:] = 0.0
-        n_cycles += 1
+        self.n_cycles += 1
+
+
+def _replay(sf, orc, d, n_keep, n_lanczos, n_iter, label):
+    gsys, osys = sf.System.from_dict(d), orc.System.from_dict(d)
+    lz = sf.Lanczos(gsys, np.array([0], dtype=np.uint64), np.array([1.0]), n_keep, n_lanczos,
+                    max_iter=n_iter)
+    rp = Replay(orc, osys, _vec(sf, lz), n_keep, n_lanczos, label)
+    for _ in range(n_iter):
+        info = lz.step()
+        Tg, Sg = lz.matrices()
+        rp.step(info, Tg, Sg, _vec(sf, lz))
     lz.close()
     gsys.close()
-    print(f"{label}: {n_iter} steps, {n_cycles} cycle ends, energies {energies}, "
-          f"kept-set differences at the cut {n_diff}")
-    return energies
+    print(f"{label}: {n_iter} steps, {rp.n_cycles} cycle ends, energies {rp.energies}, "
+          f"kept-set differences at the cut {rp.n_diff}")
+    return rp.energies
 
 
 def test_replay_closed_shell_cfg0(sf, orc):
