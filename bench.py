@@ -660,6 +660,10 @@ def run_ours(a):
                                      stream, "same system as the headline at N_d = 1e5"),
             "cfg4_rdm": rdm_row(sf, stream),
             "cfg3_scan": scan_study(sf, 1.0, a.nlanczos, 3, 8),
+            # the same 32 instances with caps cut 100-fold (1e3 determinants each): every
+            # instance step is a few milliseconds of kernels and launch latency, the
+            # regime where stepping the instances concurrently pays
+            "cfg3_scan_caps_x0.01": scan_study(sf, 0.01, a.nlanczos, 3, 10),
         }
     issue = pipe_rates(sf) if rank == 0 and not a.no_workloads else None
 

@@ -393,8 +393,9 @@ sfci_status sfci_debug_excitations(const sfci_system *sys, const uint64_t *rank,
  * fused multiply-add, 1 float64 add, 2 float64 multiply, 3 float32 fused
  * multiply-add, 4 64-bit integer multiply-add, 5 64-bit integer atomic add on
  * shared memory, 6 32-bit integer atomic add on shared memory, 7 64-bit
- * compare-and-swap on shared memory.  iters in [1, 2^30] loop trips per
- * thread (8 operations each for kinds 0-4, 2 for 5-7); workspace: 8 bytes of
+ * compare-and-swap on shared memory, 8 float32 atomic add on shared memory.
+ * iters in [1, 2^30] loop trips per thread (8 operations each for kinds 0-4,
+ * 2 for 5-8); workspace: 8 bytes of
  * device memory.  Not part of the method: it gives the issue-rate ceilings
  * against which the kernels' counters are read.  Synchronises the stream. */
 sfci_status sfci_debug_pipe_rate(int kind, int64_t iters, void *workspace, double *ops_per_s,

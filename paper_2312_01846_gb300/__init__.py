@@ -472,7 +472,7 @@ class Scan:
 
 
 PIPE_KINDS = ("fp64_fma", "fp64_add", "fp64_mul", "fp32_fma", "int64_mad", "smem_atomic_add_u64",
-              "smem_atomic_add_u32", "smem_cas_u64")
+              "smem_atomic_add_u32", "smem_cas_u64", "smem_atomic_add_f32")
 
 
 def pipe_rate(kind, iters=1 << 14, stream=None):

@@ -495,6 +495,14 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                 } else {
                     keep = kMode != kModeBucket;
                 }
+                // a hop whose integrals (ai|bj) are all exactly zero gives only zero
+                // opposite-spin doubles, which are dropped anyway: skipped (exact;
+                // e.g. the on-site interaction of a Hubbard model); the debug mode
+                // lists every element
+                if (keep && kMode != kModeDebug) {
+                    const int io = x / d.va, iv = x - io * d.va;
+                    keep = __double_as_longlong(__ldg(&d.bound_ab[virA[iv] * n + occA[io]])) != 0ll;
+                }
             }
             const unsigned bal = __ballot_sync(kFull, keep);
             if (keep) {
@@ -581,6 +589,8 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                 if (kMode == kModeBucket && o.b.eps_elem > 0.0 &&
                     fabs(c) * __ldg(&d.bound_ss[i * n + j]) < o.b.eps_elem)
                     continue;  // heat-bath style screen: no (a, b) of this pair survives
+                if (kMode != kModeDebug && __double_as_longlong(__ldg(&d.bound_ss[i * n + j])) == 0ll)
+                    continue;  // every (ai|bj) - (aj|bi) of this pair is exactly zero
                 const unsigned long long rem = str ^ (1ull << i) ^ (1ull << j);
                 pair_prefix(occ, M, io, jo, bt, ks, pre);
                 for (int q0 = 0; q0 < npv; q0 += 32 * kU) {

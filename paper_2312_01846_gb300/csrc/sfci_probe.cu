@@ -14,6 +14,7 @@
 //   kind 5  64-bit integer atomic add on shared memory (distinct addresses per lane)
 //   kind 6  32-bit integer atomic add on shared memory
 //   kind 7  64-bit compare-and-swap on shared memory (always succeeding)
+//   kind 8  float32 atomic add on shared memory
 // One launch of 152 x 8 CTAs of 256 threads per measurement, timed with CUDA
 // events on the given stream after one warm-up launch.  Result: operations
 // (lane operations) per second.
@@ -29,9 +30,11 @@ template <int kKind>
 __global__ void __launch_bounds__(kPT) probe_kernel(long long iters, double seed, unsigned long long *sink) {
     __shared__ unsigned long long sh64[kPT * 2];
     __shared__ unsigned sh32[kPT * 2];
+    __shared__ float shf[kPT * 2];
     const int t = threadIdx.x;
     sh64[t] = sh64[t + kPT] = 0ull;
     sh32[t] = sh32[t + kPT] = 0u;
+    shf[t] = shf[t + kPT] = 0.f;
     __syncthreads();
     double a[kChains];
     float f[kChains];
@@ -61,6 +64,10 @@ __global__ void __launch_bounds__(kPT) probe_kernel(long long iters, double seed
             atomicAdd(&sh32[t], 1u);
             atomicAdd(&sh32[t + kPT], 3u);
         }
+        if constexpr (kKind == 8) {
+            atomicAdd(&shf[t], 1.0f);
+            atomicAdd(&shf[t + kPT], 3.0f);
+        }
         if constexpr (kKind == 7) {
             const unsigned long long c0 = sh64[t];
             atomicCAS(&sh64[t], c0, c0 + 1ull);
@@ -68,7 +75,8 @@ __global__ void __launch_bounds__(kPT) probe_kernel(long long iters, double seed
             atomicCAS(&sh64[t + kPT], c1, c1 + 1ull);
         }
     }
-    unsigned long long r = sh64[t] + sh64[t + kPT] + sh32[t] + sh32[t + kPT];
+    unsigned long long r = sh64[t] + sh64[t + kPT] + sh32[t] + sh32[t + kPT] +
+                           __float_as_uint(shf[t]) + __float_as_uint(shf[t + kPT]);
 #pragma unroll
     for (int k = 0; k < kChains; ++k)
         r += (unsigned long long)__double_as_longlong(a[k]) + __float_as_uint(f[k]) + u[k];
@@ -108,8 +116,8 @@ extern "C" {
 
 sfci_status sfci_debug_pipe_rate(int kind, int64_t iters, void *workspace, double *ops_per_s,
                                  void *stream) {
-    if (kind < 0 || kind > 7 || iters < 1 || iters > (1ll << 30) || !workspace || !ops_per_s) {
-        set_error("need kind in 0..7, 1 <= iters <= 2^30, a device workspace and a host result");
+    if (kind < 0 || kind > 8 || iters < 1 || iters > (1ll << 30) || !workspace || !ops_per_s) {
+        set_error("need kind in 0..8, 1 <= iters <= 2^30, a device workspace and a host result");
         return SFCI_E_INVALID;
     }
     int dev = 0, n_sm = 0;
@@ -128,7 +136,8 @@ sfci_status sfci_debug_pipe_rate(int kind, int64_t iters, void *workspace, doubl
         case 4: e = run_probe<4>(iters, grid, st, sink, &ms); break;
         case 5: e = run_probe<5>(iters, grid, st, sink, &ms); break;
         case 6: e = run_probe<6>(iters, grid, st, sink, &ms); break;
-        default: e = run_probe<7>(iters, grid, st, sink, &ms); break;
+        case 7: e = run_probe<7>(iters, grid, st, sink, &ms); break;
+        default: e = run_probe<8>(iters, grid, st, sink, &ms); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "pipe-rate probe");
     const double per_iter = kind <= 4 ? (double)kChains : 2.0;  // lane operations per thread and iteration
