@@ -71,10 +71,9 @@ typedef struct sfci_system sfci_system; /* opaque */
 
 /* sfci_system_create flags */
 /* Off-diagonal Slater-Condon elements (singles and doubles) from float32
- * copies of h and g, with float32 sums for the singles, and their products
- * element * c_D in float32 (c_D rounded to float32; float64 work runs on the
- * chip's narrowest pipe).  The diagonal and its product, the accumulation of
- * sigma, the dots and the eigensolve stay float64.  Not in the paper (which works in float64): a
+ * copies of h and g, with float32 sums for the singles.  The diagonal, the
+ * product element * c_D, the accumulation of sigma, the dots and the
+ * eigensolve stay float64.  Not in the paper (which works in float64): a
  * precision option whose energy error against the float64 path is measured
  * per result, not bounded a priori. */
 #define SFCI_FP32_ELEMENTS 1u

@@ -54,37 +54,6 @@ inline size_t emit_smem_bytes_w(const SysDev &d, int warps) {
     return block_smem(d) + size_t(warps) * warp_smem(d);
 }
 
-// A float32 as a float64, exactly, by integer operations (float64 work runs
-// on the chip's narrowest pipe; the conversion instruction would use it);
-// float32 subnormals go through the conversion (rare).
-__device__ __forceinline__ double widen_f32(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned ef = (u >> 23) & 0xFFu;
-    if (ef == 0u && (u & 0x7FFFFFu)) return (double)f;
-    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-    const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
-    const unsigned long long e = ef == 0u ? 0ull : (ef == 255u ? 0x7FFull : (unsigned long long)(ef + 896u));
-    return __longlong_as_double((long long)(sign | (e << 52) | m));
-}
-
-// the inverse of widen_f32 for a float64 holding a float32 value (normal, zero
-// or infinite); any other float64 through the conversion
-__device__ __forceinline__ float narrow_f32(double d) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    const unsigned ed = (unsigned)((b >> 52) & 0x7FFull);
-    if (ed != 0u && ed != 0x7FFu && (ed < 897u || ed > 1150u)) return __double2float_rn(d);
-    const unsigned sign = (unsigned)(b >> 63) << 31;
-    const unsigned ef = ed == 0u ? 0u : (ed == 0x7FFu ? 255u : ed - 896u);
-    return __uint_as_float(sign | (ef << 23) | (unsigned)((b >> 29) & 0x7FFFFFull));
-}
-
-// the intermediate element <D'|H|D> c_D: float64 product, or with float32
-// elements (SFCI_FP32_ELEMENTS) a float32 product of the element and c_D
-// rounded to float32, widened exactly
-__device__ __forceinline__ double scaled(double e, double c, float c32, bool f32) {
-    return f32 ? widen_f32(__fmul_rn(narrow_f32(e), c32)) : __dmul_rn(e, c);
-}
-
 // single element h_ai + sum_{k occ alpha} (ai|kk) + sum_{k occ beta} (ai|kk)
 //                 - sum_{k occ same spin} (ak|ki), source occupations
 __device__ __forceinline__ double single_element(const SysDev &d, int i, int a,
@@ -132,7 +101,7 @@ __device__ __forceinline__ double single_element_f32(const SysDev &d, int i, int
         int o = occS[k];
         v = __fsub_rn(v, __ldg(&d.gf[(size_t(a * n + o) * n + o) * n + i]));
     }
-    return widen_f32(v);
+    return (double)v;
 }
 
 // <D|H|D> = e_core + sum_k h_kk + 1/2 sum_{k,l} (kk|ll) - 1/2 sum_{k,l same spin} (kl|lk)
@@ -357,11 +326,9 @@ template <int kMode>
 __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
                                            const unsigned long long *ha, const unsigned long long *hb,
                                            const unsigned *bk, const double *e, const long long *di,
-                                           long long s, double c, float c32, bool f32, bool diag_first,
-                                           unsigned long long cb, unsigned &inserted,
-                                           unsigned long long *cur, long long single = -1) {
-    // element k of lane 0 is the diagonal when diag_first: its product stays float64
-    const bool d0 = diag_first && (threadIdx.x & 31) == 0;
+                                           long long s, double c, unsigned long long cb,
+                                           unsigned &inserted, unsigned long long *cur,
+                                           long long single = -1) {
     if constexpr (kMode == kModeDebug) {
 #pragma unroll
         for (int k = 0; k < kU; ++k)
@@ -370,7 +337,7 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
 #pragma unroll
         for (int k = 0; k < kU; ++k) {
             if (!want[k]) continue;
-            const double v = scaled(e[k], c, c32, f32 && !(k == 0 && d0));
+            const double v = __dmul_rn(e[k], c);
             if (!nonzero(v)) continue;
             if (o.t.acc) table_add_exact(o.t, ha[k] * cb + hb[k], v, inserted);
             else table_add(o.t, ha[k] * cb + hb[k], v, inserted);
@@ -386,7 +353,7 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
             tg[k] = 0;
             v[k] = 0.0;
             if (!want[k]) continue;
-            v[k] = scaled(e[k], c, c32, f32 && !(k == 0 && d0));
+            v[k] = __dmul_rn(e[k], c);
             tg[k] = ha[k] * cb + hb[k];
             ok[k] = nonzero(v[k]);
         }
@@ -484,7 +451,6 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
     for (long long s = gw; s < n_in; s += nw) {
         const unsigned long long r = in_rank[s];
         const double c = kMode == kModeDebug ? 1.0 : in_coef[s];
-        const float c32 = f32 ? __double2float_rn(c) : 0.f;  // once per source
         const unsigned long long hA = r / cb, hB = r - hA * cb;
         const unsigned long long alpha = string_unrank_warp(hA, n, d.na, bt, ks);
         const unsigned long long beta = string_unrank_warp(hB, n, d.nb, bt, ks);
@@ -584,7 +550,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     e[k] = flip(F, offA1[x] >> 31);
                 }
             }
-            emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, c32, f32, x0 == -1, cb, inserted, ocur);
+            emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur);
         }
         long long off = base + 1 + d.sa;
         // beta singles (all in row hA)
@@ -601,7 +567,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     want[k] = true, ha[k] = hA, hb[k] = rankB1[y], di[k] = off + y;
                     e[k] = flip(F, offB1[y] >> 31);
                 }
-                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, c32, f32, false, cb, inserted, ocur, self_single);
+                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, self_single);
             }
         }
         off += d.sb;
@@ -644,12 +610,11 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                         want[k] = true, ha[k] = ta, hb[k] = tb, di[k] = off + (long long)p * npv + q;
                         const size_t x1 = (size_t(a * n + i) * n + b) * n + j;
                         const size_t x2 = (size_t(a * n + j) * n + b) * n + i;
-                        const double gd = f32 ? widen_f32(__fsub_rn(__ldg(&d.gf[x1]), __ldg(&d.gf[x2])))
+                        const double gd = f32 ? (double)__fsub_rn(__ldg(&d.gf[x1]), __ldg(&d.gf[x2]))
                                               : __dsub_rn(__ldg(&g[x1]), __ldg(&g[x2]));
                         e[k] = flip(gd, unsigned(s1 ^ s2));
                     }
-                    emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, c32, f32, false, cb, inserted, ocur,
-                                      spin ? self_single : -1);
+                    emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, spin ? self_single : -1);
                 }
                 __syncwarp();
             }
@@ -673,7 +638,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                         if (row_wanted<kMode>(o, rc, ra, hbv, bk[k])) {
                             const unsigned oa = offA1[x], ob = offB1[cy];
                             const unsigned gi = (oa & 0x7fffffffu) + (ob & 0x7fffffffu);
-                            const double gv = f32 ? widen_f32(__ldg(&d.gf[gi])) : __ldg(&g[gi]);
+                            const double gv = f32 ? (double)__ldg(&d.gf[gi]) : __ldg(&g[gi]);
                             want[k] = true, ha[k] = ra, hb[k] = hbv;
                             di[k] = off + (long long)x * d.sb + cy;
                             e[k] = flip(gv, (oa ^ ob) >> 31);
@@ -682,7 +647,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     cy += 32;
                     while (cy >= d.sb) cy -= d.sb, ++cx;
                 }
-                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, c32, f32, false, cb, inserted, ocur,
+                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur,
                                   kMode == kModeBucket ? round_single(want, bk) : -1);
             }
         }
