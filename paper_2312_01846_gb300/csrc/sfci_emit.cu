@@ -43,11 +43,15 @@ __host__ __device__ inline size_t block_smem(const SysDev &d) {
     return align16(size_t(d.n + 1) * d.ks * 8) + align16(size_t(d.n_pairs) * 2);
 }
 
+// Opposite-spin doubles of an alpha hop whose target row has at most this many
+// buckets reserve their places per bucket once per hop (bins below).
+constexpr int kHopBins = 32;
+
 // per warp: overflow chunk cursor (2 u64), rankA1, rankB1 (u64), prefix sums
-// (3 ks u64), hopRC (u64 per alpha hop), offA1, offB1 (u32), hopX (u16 per
-// alpha hop), occupation lists (256 B)
+// (3 ks u64), offA1, offB1, mixB (u32), the hop's bins (4 x kHopBins u32), hopX
+// (u16 per alpha hop), yoff (u16 per beta hop), occupation lists (256 B)
 __host__ __device__ inline size_t warp_smem(const SysDev &d) {
-    return align16(16 + size_t(d.sa + d.sb) * 12 + size_t(d.sa) * 10 + size_t(3 * d.ks) * 8 + 256);
+    return align16(16 + size_t(d.sa) * 14 + size_t(d.sb) * 18 + size_t(3 * d.ks) * 8 + size_t(kHopBins) * 16 + 256);
 }
 
 inline size_t emit_smem_bytes_w(const SysDev &d, int warps) {
@@ -428,11 +432,16 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
     unsigned long long *rankA1 = ocur + 2;
     unsigned long long *rankB1 = rankA1 + d.sa;
     unsigned long long *pre = rankB1 + d.sb;  // prefix sums A0 | A1 | A2, ks each
-    unsigned long long *hopRC = pre + 3 * ks;  // bucket map entry of each kept alpha hop's row
-    unsigned *offA1 = reinterpret_cast<unsigned *>(hopRC + d.sa);
+    unsigned *offA1 = reinterpret_cast<unsigned *>(pre + 3 * ks);
     unsigned *offB1 = offA1 + d.sa;
-    unsigned short *hopX = reinterpret_cast<unsigned short *>(offB1 + d.sb);  // kept alpha hops
-    unsigned char *occA = reinterpret_cast<unsigned char *>(hopX + d.sa);
+    unsigned *mixB = offB1 + d.sb;  // top 32 bits of mix64 of each beta hop's index (its bucket in a split row)
+    unsigned *hcnt = mixB + d.sb;   // per bucket of the current alpha hop's row: elements,
+    unsigned *hbase = hcnt + kHopBins;  // first reserved place,
+    unsigned *hs0 = hbase + kHopBins;   // region start (units of 4 slots), region capacity
+    unsigned *hcap = hs0 + kHopBins;
+    unsigned short *hopX = reinterpret_cast<unsigned short *>(hcap + kHopBins);  // kept alpha hops
+    unsigned short *yoff = hopX + d.sa;  // place of each beta hop's element within its bucket's share
+    unsigned char *occA = reinterpret_cast<unsigned char *>(yoff + d.sb);
     unsigned char *virA = occA + 64, *occB = occA + 128, *virB = occA + 192;
     const unsigned char *pOA = pairs + 2 * d.pair_off[0], *pVA = pairs + 2 * d.pair_off[1];
     const unsigned char *pOB = pairs + 2 * d.pair_off[2], *pVB = pairs + 2 * d.pair_off[3];
@@ -473,20 +482,19 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             const unsigned sg = parity64(beta & between_mask(j, b));
             rankB1[y] = string_rank(beta ^ (1ull << j) ^ (1ull << b), bt, ks);
             offB1[y] = unsigned(b * n + j) | (sg << 31);
+            if (kMode == kModeBucket) mixB[y] = (unsigned)(mix64(rankB1[y]) >> 32);
         }
         __syncwarp();
         // alpha hops whose target row can hold buckets of this pass (every hop
-        // outside bucket mode), compacted, with their row's bucket map entry
+        // outside bucket mode), compacted
         int m_hops = 0;
         for (int x0 = 0; x0 < d.sa; x0 += 32) {
             const int x = x0 + lane;
             bool keep = false;
-            unsigned long long rcv = 0;
             if (x < d.sa) {
                 if (kMode == kModeBucket && rankA1[x] >= o.b.row_lo && rankA1[x] <= o.b.row_hi) {
                     const RowCtx rc = row_ctx(o.b, rankA1[x]);
                     keep = ctx_in_pass(o.b, rc);
-                    rcv = (unsigned long long)rc.first << 32 | rc.ns;
                     // heat-bath style screen: no beta hop can lift |(ai|bj) c| to eps
                     if (keep && o.b.eps_elem > 0.0) {
                         const int io = x / d.va, iv = x - io * d.va;
@@ -505,11 +513,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                 }
             }
             const unsigned bal = __ballot_sync(kFull, keep);
-            if (keep) {
-                const int pos = m_hops + __popc(bal & ((1u << lane) - 1u));
-                hopX[pos] = (unsigned short)x;
-                hopRC[pos] = rcv;
-            }
+            if (keep) hopX[m_hops + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)x;
             m_hops += __popc(bal);
         }
         __syncwarp();
@@ -620,9 +624,83 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             }
             off += (long long)npo * npv;
         }
-        // opposite-spin doubles, flattened over (kept alpha hop, beta hop) pairs:
-        // lane t of the warp takes pairs t, t + 32, ... so every round is full
-        if (d.sb > 0 && m_hops > 0) {
+        // opposite-spin doubles.  Bucket mode, one kept alpha hop at a time: when
+        // the hop's target row has at most kHopBins buckets, its sb elements are
+        // counted per bucket (shared-memory atomics), each bucket's places are
+        // reserved with one atomic and its region read once, and every element
+        // goes straight to its place (a zero product keeps its place as a
+        // zero-valued element); rows split further take rounds with per-round
+        // reservations.  Other modes: flattened over (kept alpha hop, beta hop)
+        // pairs, lane t taking pairs t, t + 32, ... so every round is full.
+        if (kMode == kModeBucket && d.sb > 0) {
+            for (int cx = 0; cx < m_hops; ++cx) {
+                const int x = hopX[cx];
+                const unsigned long long ra = rankA1[x];
+                const RowCtx rc = row_ctx(o.b, ra);
+                const unsigned oa = offA1[x];
+                const unsigned long long rbase = ra * cb;
+                if (rc.ns != 0xffffffffu && rc.ns <= (unsigned)kHopBins) {
+                    const unsigned ns = rc.ns, first = rc.first;
+                    if ((unsigned)lane < ns) hcnt[lane] = 0u;
+                    __syncwarp();
+                    for (int y = lane; y < d.sb; y += 32) {
+                        const unsigned bin = ns == 1u ? 0u : __umulhi(mixB[y], ns);
+                        yoff[y] = in_pass(o.b, first + bin) ? (unsigned short)atomicAdd(&hcnt[bin], 1u)
+                                                            : (unsigned short)0xffffu;
+                    }
+                    __syncwarp();
+                    if ((unsigned)lane < ns) {
+                        const unsigned cnt = hcnt[lane];
+                        unsigned base = 0u, s0 = 0u, s1 = 0u;
+                        if (cnt) {
+                            const unsigned b = first + lane;
+                            base = atomicAdd(&o.b.count[b], cnt);
+                            s0 = __ldg(&o.b.start4[b]);
+                            s1 = __ldg(&o.b.start4[b + 1]);
+                        }
+                        hbase[lane] = base, hs0[lane] = s0, hcap[lane] = (s1 - s0) << 2;
+                    }
+                    __syncwarp();
+                    ulonglong2 *elem = reinterpret_cast<ulonglong2 *>(o.b.elem);
+                    for (int y0 = 0; y0 < d.sb; y0 += 32) {
+                        const int y = y0 + lane;
+                        bool of = false;
+                        ulonglong2 sl = make_ulonglong2(0ull, 0ull);
+                        if (y < d.sb && yoff[y] != 0xffffu) {
+                            const unsigned bin = ns == 1u ? 0u : __umulhi(mixB[y], ns);
+                            const unsigned ob = offB1[y];
+                            const unsigned gi = (oa & 0x7fffffffu) + (ob & 0x7fffffffu);
+                            const double gv = f32 ? (double)__ldg(&d.gf[gi]) : __ldg(&g[gi]);
+                            double v = __dmul_rn(flip(gv, (oa ^ ob) >> 31), c);
+                            if (!nonzero(v) || (o.b.eps_elem > 0.0 && fabs(v) < o.b.eps_elem)) v = 0.0;
+                            sl = make_ulonglong2(rbase + rankB1[y], (unsigned long long)__double_as_longlong(v));
+                            const unsigned pos = hbase[bin] + yoff[y];
+                            if (pos < hcap[bin]) __stcs(elem + ((unsigned long long)hs0[bin] << 2) + pos, sl);
+                            else of = true;
+                        }
+                        overflow_append(o.b, of, sl, ocur);
+                    }
+                    __syncwarp();  // the bins are reused by the next hop
+                } else {
+                    for (int y0 = 0; y0 < d.sb; y0 += 32 * kU) {
+                        SFCI_CLEAR();
+#pragma unroll
+                        for (int k = 0; k < kU; ++k) {
+                            const int y = y0 + 32 * k + lane;
+                            if (y >= d.sb) continue;
+                            const unsigned long long hbv = rankB1[y];
+                            if (!row_wanted<kMode>(o, rc, ra, hbv, bk[k])) continue;
+                            const unsigned ob = offB1[y];
+                            const unsigned gi = (oa & 0x7fffffffu) + (ob & 0x7fffffffu);
+                            const double gv = f32 ? (double)__ldg(&d.gf[gi]) : __ldg(&g[gi]);
+                            want[k] = true, ha[k] = ra, hb[k] = hbv;
+                            e[k] = flip(gv, (oa ^ ob) >> 31);
+                        }
+                        emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, -1);
+                    }
+                }
+            }
+        } else if (d.sb > 0 && m_hops > 0) {
             const long long nab = (long long)m_hops * d.sb;
             int cx = lane / d.sb;
             int cy = lane - cx * d.sb;
@@ -633,8 +711,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     if (t0 + 32 * k + lane < nab) {
                         const int x = hopX[cx];
                         const unsigned long long ra = rankA1[x], hbv = rankB1[cy];
-                        const unsigned long long rcv = hopRC[cx];
-                        const RowCtx rc{(unsigned)(rcv >> 32), (unsigned)rcv};
+                        const RowCtx rc{0u, 0u};  // not used outside bucket mode
                         if (row_wanted<kMode>(o, rc, ra, hbv, bk[k])) {
                             const unsigned oa = offA1[x], ob = offB1[cy];
                             const unsigned gi = (oa & 0x7fffffffu) + (ob & 0x7fffffffu);
