@@ -34,7 +34,8 @@ namespace {
 #define SFCI_MERGE_THREADS 256
 #endif
 constexpr int kMT = SFCI_MERGE_THREADS;  // merge CTA threads
-constexpr int kPre = 8;              // elements each thread loads before inserting
+constexpr int kPre = 4;              // elements each thread loads before inserting (4: more unrolling
+                                     // outgrows the instruction cache; measured)
 
 // slot in the shared-memory table.  Hash mode: the mix64 bits just below
 // those that chose the bucket.  Row mode: a split row's bucket was chosen by
