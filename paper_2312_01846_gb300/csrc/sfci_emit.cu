@@ -144,7 +144,7 @@ __device__ __forceinline__ bool nonzero(double v) {
     return ((unsigned long long)__double_as_longlong(v) << 1) != 0ull;
 }
 
-constexpr int kU = 2;  // elements each lane carries per reservation round
+constexpr int kU = 1;  // elements each lane carries per reservation round (2 and 3 measured slower)
 
 __device__ __forceinline__ bool in_pass(const BucketOut &B, unsigned b) { return b >= B.lo && b < B.hi; }
 
