@@ -26,9 +26,10 @@
 //   a6  element * c_D, exact zeros dropped, then appended to the target's
 //       bucket (warp-aggregated reservation, one atomic per bucket and round)
 //       or added into the table.
-// The lanes of the warp stride over the excitations of each class, two
-// elements per lane per round, so a warp issues 64 independent elements at a
-// time.
+// The lanes of the warp stride over the excitations of each class, one element
+// per lane per round; the opposite-spin doubles of an alpha hop whose target
+// row has at most kHopBins buckets reserve their places per bucket once for
+// the whole hop.
 #include "sfci_internal.cuh"
 
 namespace sfci {
