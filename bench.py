@@ -40,7 +40,11 @@ BYTES_PER_ELEMENT = 32  # 16 B intermediate element written + 16 B read back by 
 # DRAM bytes per connected element that ncu measured for emit_kernel + merge_kernel
 # together (dram__bytes_read.sum + dram__bytes_write.sum of one launch each on the same
 # workload at N_d = 5e3, 1.5362e8 elements, one pass); scaled by the elements of a step
-MEASURED_DRAM_BYTES_PER_ELEMENT = (0.042551 + 2.432639 + 2.465470 + 0.004218) * 1e9 / 1.5362e8
+MEASURED_DRAM_BYTES_PER_ELEMENT = (0.053608 + 2.438130 + 2.467469 + 0.004204) * 1e9 / 1.5362e8
+# warp instructions per connected element (smsp__inst_executed.sum of the same captures) and
+# the issue ceiling: 152 SMs x 4 schedulers x one warp instruction per clock at 2070 MHz
+MEASURED_WARP_INST_PER_ELEMENT = {"emit_kernel": 1165891164 / 1.5362e8, "merge_kernel": 1999301422 / 1.5362e8}
+ISSUE_PEAK_WARP_INST_PER_S = 152 * 4 * 2.07e9
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -591,7 +595,17 @@ def run_ours(a):
                 "buckets_log2": max(i["n_buckets_log2"] for i in infos),
                 "elements_per_launch": el_per_launch,
                 "nonzero_elements_per_launch": statistics.mean(i["n_emitted"] for i in infos),
-                "sigma_share_of_step": sum(i["ms_sigma"] for i in infos) / ms}
+                "sigma_share_of_step": sum(i["ms_sigma"] for i in infos) / ms,
+                # the kernels are bound by instruction issue and latency, not by DRAM: the
+                # issue-slot view, with warp instructions per element from the N_d = 5e3
+                # captures (at N_d = 1e6 entries repeat more, so the merge streams out fewer
+                # entries per element and this overstates its count)
+                "issue": {kname: {"warp_inst_per_element": ipe,
+                                  "achieved_warp_inst_per_s": ipe * el_per_launch / (ms_k * 1e-3),
+                                  "peak_warp_inst_per_s": ISSUE_PEAK_WARP_INST_PER_S,
+                                  "frac": ipe * el_per_launch / (ms_k * 1e-3) / ISSUE_PEAK_WARP_INST_PER_S}
+                          for kname, ipe, ms_k in (("emit_kernel", MEASURED_WARP_INST_PER_ELEMENT["emit_kernel"], ms_emit),
+                                                   ("merge_kernel", MEASURED_WARP_INST_PER_ELEMENT["merge_kernel"], ms_merge))}}
 
     # end to end through the public API with host buffers, chained: each step
     # copies its input vector w_i host -> device and hands it to the solver
