@@ -258,6 +258,8 @@ typedef struct sfci_step_info {
     double ms_alloc;       /* of ms_plan: device buffer (re)allocation               */
     int64_t n_emitted;     /* intermediate elements generated for sigma_i and merged:
                               the non-zero products of n_elements                */
+    int64_t n_alpha_runs;  /* runs of consecutive entries of w_i that share alpha
+                              (0: not counted, hash mode)                         */
 } sfci_step_info;
 
 typedef struct sfci_lanczos sfci_lanczos; /* opaque; owns w_0..w_{N_L-1}, T, S, table */

@@ -52,7 +52,8 @@ class StepInfo(C.Structure):
                 ("n_passes", C.c_int32), ("n_buckets_log2", C.c_int32),
                 ("tau", C.c_double), ("cut", C.c_double), ("redo", C.c_int32), ("bucket_redo", C.c_int32),
                 ("pass_budget_gb", C.c_double), ("regions_gb", C.c_double), ("free_gb", C.c_double),
-                ("n_overflow", C.c_int64), ("ms_alloc", C.c_double), ("n_emitted", C.c_int64)]
+                ("n_overflow", C.c_int64), ("ms_alloc", C.c_double), ("n_emitted", C.c_int64),
+                ("n_alpha_runs", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -264,6 +264,7 @@ sfci_status sfci_system_create(sfci_system **out, int n, int na, int nb, const d
     }
     d.bound_ab = reinterpret_cast<const double *>(blk + off_bab);
     d.bound_ss = reinterpret_cast<const double *>(blk + off_bss);
+    d.ss_any = std::any_of(bss.begin(), bss.end(), [](double x) { return x != 0.0; }) ? 1 : 0;
     s->d = d;
     s->dev_block = blk;
     *out = s;

@@ -30,6 +30,8 @@
 // per lane per round; the opposite-spin doubles of an alpha hop whose target
 // row has at most kHopBins buckets reserve their places per bucket once for
 // the whole hop.
+#include <algorithm>
+
 #include "sfci_internal.cuh"
 
 namespace sfci {
@@ -584,7 +586,9 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             const unsigned char *po = spin ? pOB : pOA, *pv = spin ? pVB : pVA;
             const int npo = spin ? d.po_b : d.po_a, npv = spin ? d.pv_b : d.pv_a;
             const int M = spin ? d.nb : d.na;
-            if (spin == 1 && !self_row) {  // beta-beta doubles stay in row hA
+            // beta-beta doubles stay in row hA; alpha-alpha doubles go by runs of
+            // sources sharing alpha (emit_aa_kernel) when o.b.aa_runs is set
+            if ((spin == 1 && !self_row) || (spin == 0 && kMode == kModeBucket && o.b.aa_runs)) {
                 off += (long long)npo * npv;
                 continue;
             }
@@ -742,15 +746,191 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
     }
 }
 
+// Live alpha-alpha excitations of a run waiting for their elements: a ring
+// of kAaQ entries per warp (target row, its first bucket and bucket count,
+// unscaled element).
+constexpr int kAaQ = 64;
+
+// per warp: overflow chunk cursor (2 u64), prefix sums (3 ks u64), the queue
+// (kAaQ x 24 B), occupation lists (256 B)
+__host__ __device__ inline size_t aa_warp_smem(const SysDev &d) {
+    return align16(16 + size_t(3 * d.ks) * 8 + size_t(kAaQ) * 24 + 256);
+}
+
+// Alpha-alpha doubles of bucket mode, by runs of sources sharing alpha.  The
+// input is sorted by rank, alpha-major, so the determinants with one alpha
+// string are consecutive; their alpha-alpha doubles reach the same target rows
+// with the same integrals and signs and differ only in the beta column and the
+// coefficient.  A work unit is a window of 32 consecutive sources and one of
+// n_groups slices of the occupied pairs (i, j) (several slices when the
+// windows alone are too few to fill the GPU); the warp splits the window into
+// its runs.  For a run of length L, the warp first takes the
+// excitations (i, j) -> (a, b) one per lane: target row, its buckets (one
+// row-map read) and the element; those whose row can hold buckets of this
+// pass and whose element is not zero join a queue.  Rounds of 32 (excitation,
+// source) items then leave the queue (lane t: excitation t / L, source
+// t mod L, in queue order), so a round is full whatever the share of rows in
+// the pass, and the lanes of one excitation share a row and often a bucket
+// (one reservation, one run of places).
+__global__ void __launch_bounds__(kEmitThreads, 4)
+emit_aa_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
+               const double *__restrict__ in_coef, long long n_in, int n_groups, const EmitOut o) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int n = d.n, ks = d.ks;
+    unsigned long long *bt = reinterpret_cast<unsigned long long *>(sm);
+    unsigned char *pairs = sm + align16(size_t(n + 1) * ks * 8);
+    for (int i = threadIdx.x; i < (n + 1) * ks; i += blockDim.x) bt[i] = d.binom[i];
+    for (int i = threadIdx.x; i < 2 * d.n_pairs; i += blockDim.x) pairs[i] = d.pairs[i];
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned char *wb = sm + block_smem(d) + size_t(warp) * aa_warp_smem(d);
+    unsigned long long *ocur = reinterpret_cast<unsigned long long *>(wb);
+    unsigned long long *pre = ocur + 2;
+    unsigned long long *qh = pre + 3 * ks;  // queue: target row
+    double *qe = reinterpret_cast<double *>(qh + kAaQ);  // unscaled element
+    unsigned *qf = reinterpret_cast<unsigned *>(qe + kAaQ);  // first bucket of the row
+    unsigned *qn = qf + kAaQ;  // bucket count of the row (~0: hash mode)
+    unsigned char *occA = reinterpret_cast<unsigned char *>(qn + kAaQ);
+    unsigned char *virA = occA + 64, *occB = occA + 128, *virB = occA + 192;
+    const unsigned char *pOA = pairs + 2 * d.pair_off[0], *pVA = pairs + 2 * d.pair_off[1];
+    const unsigned long long cb = d.cb;
+    const double *__restrict__ g = d.g;
+    const bool f32 = d.gf != nullptr;
+    const int npo = d.po_a, npv = d.pv_a, M = d.na;
+
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned inserted = 0;
+    if (lane == 0) ocur[0] = 0ull, ocur[1] = 0ull;
+    __syncwarp();
+
+    const long long n_units = (n_in + 31) / 32 * n_groups;
+    for (long long u = gw; u < n_units; u += nw) {
+        const long long win = u / n_groups;
+        const int grp = (int)(u - win * n_groups);
+        const int p_lo = grp * npo / n_groups, p_hi = (grp + 1) * npo / n_groups;
+        const long long sl = win * 32 + lane;
+        const bool valid = sl < n_in;
+        const unsigned long long r = valid ? in_rank[sl] : 0ull;
+        const double cl = valid ? in_coef[sl] : 0.0;
+        const unsigned long long hAl = r / cb, hBl = r - hAl * cb;
+        const unsigned mixl = (unsigned)(mix64(hBl) >> 32);
+        const unsigned long long hAu = __shfl_up_sync(kFull, hAl, 1);
+        unsigned starts = __ballot_sync(kFull, valid && (lane == 0 || hAu != hAl));
+        const int n_valid = __popc(__ballot_sync(kFull, valid));
+        while (starts) {
+            const int s0 = __ffs(starts) - 1;
+            starts &= starts - 1u;
+            const int L = (starts ? __ffs(starts) - 1 : n_valid) - s0;
+            const unsigned long long hA = __shfl_sync(kFull, hAl, s0);
+            double cmax = (lane >= s0 && lane < s0 + L) ? fabs(cl) : 0.0;  // the run's largest |c| (screen)
+            for (int w = 16; w > 0; w >>= 1) cmax = fmax(cmax, __shfl_xor_sync(kFull, cmax, w));
+            const unsigned long long alpha = string_unrank_warp(hA, n, d.na, bt, ks);
+            build_lists(alpha, 0ull, n, occA, virA, occB, virB);
+            __syncwarp();
+            // queue state (warp-uniform): excitations pushed, items emitted; this
+            // lane's item cur + lane is excitation k, source sr of the run
+            const int dq = 32 / L, ds = 32 - dq * L;
+            unsigned qhead = 0, cur = 0;
+            int k = lane / L, sr = lane - (lane / L) * L;
+            // one round: items cur .. cur + 31 (those below qhead * L exist)
+            auto round = [&]() {
+                bool want[kU] = {false};
+                unsigned long long ha[kU] = {0ull}, hb[kU] = {0ull};
+                unsigned bk[kU] = {0u};
+                double e[kU] = {0.0};
+                long long di[kU] = {0};
+                const int src = s0 + sr;
+                const unsigned long long hbs = __shfl_sync(kFull, hBl, src);
+                const double cs = __shfl_sync(kFull, cl, src);
+                const unsigned ms = __shfl_sync(kFull, mixl, src);
+                if (cur + (unsigned)lane < qhead * (unsigned)L) {
+                    const int qi = k & (kAaQ - 1);
+                    const unsigned long long h2 = qh[qi];
+                    const unsigned ns = qn[qi], first = qf[qi];
+                    bk[0] = ns == 0xffffffffu ? bucket_ab(o.b.bk, h2, hbs)
+                                              : (ns == 1u ? first : first + __umulhi(ms, ns));
+                    want[0] = in_pass(o.b, bk[0]);
+                    ha[0] = h2, hb[0] = hbs, e[0] = qe[qi];
+                }
+                emit_round<kModeBucket>(o, want, ha, hb, bk, e, di, 0, cs, cb, inserted, ocur,
+                                        L == 32 ? round_single(want, bk) : -1);
+                cur += 32u, k += dq, sr += ds;
+                if (sr >= L) sr -= L, ++k;
+            };
+            for (int p = p_lo; p < p_hi; ++p) {
+                const int io = pOA[2 * p], jo = pOA[2 * p + 1];
+                const int i = occA[io], j = occA[jo];
+                if (o.b.eps_elem > 0.0 && cmax * __ldg(&d.bound_ss[i * n + j]) < o.b.eps_elem)
+                    continue;  // heat-bath style screen: no (a, b) of this pair survives for any source
+                if (__double_as_longlong(__ldg(&d.bound_ss[i * n + j])) == 0ll)
+                    continue;  // every (ai|bj) - (aj|bi) of this pair is exactly zero
+                const unsigned long long rem = alpha ^ (1ull << i) ^ (1ull << j);
+                pair_prefix(occA, M, io, jo, bt, ks, pre);
+                for (int q0 = 0; q0 < npv; q0 += 32) {
+                    const int q = q0 + lane;
+                    bool live = false;
+                    unsigned long long h2 = 0ull;
+                    unsigned first = 0u, ns = 0u;
+                    double ev = 0.0;
+                    if (q < npv) {
+                        const int a = virA[pVA[2 * q]], b = virA[pVA[2 * q + 1]];
+                        h2 = pair_rank(rem, a, b, M, pre, bt, ks);
+                        if (h2 >= o.b.row_lo && h2 <= o.b.row_hi) {
+                            if (!o.b.bk.rowmap) {
+                                ns = 0xffffffffu, live = true;
+                            } else {
+                                const RowCtx rc = row_ctx(o.b, h2);
+                                first = rc.first, ns = rc.ns;
+                                live = ctx_in_pass(o.b, rc);
+                            }
+                            if (live) {
+                                const int s1 = parity64(alpha & between_mask(i, a));
+                                const unsigned long long s1s = alpha ^ (1ull << i) ^ (1ull << a);
+                                const int s2 = parity64(s1s & between_mask(j, b));
+                                const size_t x1 = (size_t(a * n + i) * n + b) * n + j;
+                                const size_t x2 = (size_t(a * n + j) * n + b) * n + i;
+                                const double gd = f32 ? (double)__fsub_rn(__ldg(&d.gf[x1]), __ldg(&d.gf[x2]))
+                                                      : __dsub_rn(__ldg(&g[x1]), __ldg(&g[x2]));
+                                ev = flip(gd, unsigned(s1 ^ s2));
+                                live = nonzero(ev);
+                            }
+                        }
+                    }
+                    // the ring holds fewer than 32 / L + 1 <= 32 unfinished
+                    // excitations here, so 32 more fit; the last round's reads
+                    // are done before any lane overwrites an entry
+                    const unsigned bal = __ballot_sync(kFull, live);
+                    __syncwarp();
+                    if (live) {
+                        const int qi = (qhead + __popc(bal & lt)) & (kAaQ - 1);
+                        qh[qi] = h2, qe[qi] = ev, qf[qi] = first, qn[qi] = ns;
+                    }
+                    qhead += __popc(bal);
+                    __syncwarp();
+                    while (qhead * (unsigned)L - cur >= 32u) round();
+                }
+                __syncwarp();
+            }
+            while (cur < qhead * (unsigned)L) round();
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    ovf_pad(o.b, ocur[0], ocur[1]);
+}
+
 // weights[ha] += elements bound for row ha: the source's own row gets the
 // diagonal, its beta singles and beta-beta doubles; each alpha single's row
 // gets the single plus one element per beta hop; each alpha-alpha double's row
 // gets one element.  One warp per input determinant (per run of determinants
-// sharing alpha when nothing is screened).
+// sharing alpha when nothing is screened).  *n_runs += the number of such runs.
 __global__ void __launch_bounds__(kEmitThreads)
 row_weight_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                   const double *__restrict__ in_coef, long long n_in, double eps,
-                  unsigned long long *__restrict__ weights) {
+                  unsigned long long *__restrict__ weights, unsigned long long *__restrict__ n_runs) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int n = d.n, ks = d.ks;
     unsigned long long *bt = reinterpret_cast<unsigned long long *>(sm);
@@ -770,15 +950,18 @@ row_weight_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const unsigned char *pOB = pairs + 2 * d.pair_off[2];
+    unsigned long long runs = 0;
     for (long long s = gw; s < n_in; s += nw) {
         const unsigned long long r = in_rank[s];
         const unsigned long long hA = r / cb;
+        const bool run_start = s == 0 || in_rank[s - 1] / cb != hA;
+        runs += run_start;
         unsigned long long mult = 1;
         if (!(eps > 0.0)) {
             // without the screen the weights depend on alpha only: the first
             // source of each run of consecutive sources sharing alpha (the
             // input is sorted by rank, alpha-major) adds them times the run length
-            if (s > 0 && in_rank[s - 1] / cb == hA) continue;
+            if (!run_start) continue;
             long long e = s + 1;
             for (;;) {
                 const long long q = e + lane;
@@ -823,6 +1006,7 @@ row_weight_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank
             __syncwarp();
         }
     }
+    if (lane == 0 && runs) atomicAdd(n_runs, runs);
 }
 
 __global__ void rank_kernel(const SysDev d, const unsigned long long *a, const unsigned long long *b,
@@ -933,12 +1117,34 @@ cudaError_t launch_emit_buckets(const SysDev &d, const unsigned long long *in_ra
                                 cudaStream_t st, int warps) {
     EmitOut o{};
     o.b = b;
-    return launch_emit_impl<kModeBucket>(d, in_rank, in_coef, n_in, o, st, warps);
+    cudaError_t e = launch_emit_impl<kModeBucket>(d, in_rank, in_coef, n_in, o, st, warps);
+    // (no launch when every same-spin double is exactly zero, e.g. an on-site
+    // interaction only: the main kernel skipped them as well)
+    if (e != cudaSuccess || !b.aa_runs || !d.ss_any || n_in <= 0 || d.po_a == 0 || d.pv_a == 0) return e;
+    // alpha-alpha doubles, by runs of sources sharing alpha
+    const size_t smem = block_smem(d) + size_t(kEmitWarps) * aa_warp_smem(d);
+    e = allow_max_smem(emit_aa_kernel, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_aa_kernel, kEmitThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // about eight work units per resident warp: windows, split into slices of
+    // the occupied pairs when they are too few
+    const long long windows = (n_in + 31) / 32;
+    const long long slots = (long long)device_sms() * per_sm * kEmitWarps;
+    const int groups = (int)std::min<long long>(d.po_a, std::max<long long>(1, (8 * slots + windows - 1) / windows));
+    const long long units = windows * groups;
+    long long grid = (long long)device_sms() * per_sm;
+    if ((units + kEmitWarps - 1) / kEmitWarps < grid) grid = (units + kEmitWarps - 1) / kEmitWarps;
+    count_launch();
+    emit_aa_kernel<<<(unsigned)grid, kEmitThreads, smem, st>>>(d, in_rank, in_coef, n_in, groups, o);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_rank,
                                const double *in_coef, long long n_in, double eps_elem,
-                               unsigned long long *weights, cudaStream_t st) {
+                               unsigned long long *weights, unsigned long long *n_runs, cudaStream_t st) {
     if (n_in <= 0) return cudaSuccess;
     const size_t smem = emit_smem_bytes(d, kEmitWarps);
     cudaError_t e = allow_max_smem(row_weight_kernel, smem);
@@ -951,7 +1157,8 @@ cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_ran
     long long grid = (long long)device_sms() * per_sm;
     if (want < grid) grid = want;
     count_launch();
-    row_weight_kernel<<<(unsigned)grid, kEmitThreads, smem, st>>>(d, in_rank, in_coef, n_in, eps_elem, weights);
+    row_weight_kernel<<<(unsigned)grid, kEmitThreads, smem, st>>>(d, in_rank, in_coef, n_in, eps_elem, weights,
+                                                                   n_runs);
     return cudaGetLastError();
 }
 

@@ -139,6 +139,7 @@ struct SysDev {
     // for every (b, j); bound_ss[i*n+j] >= |(ai|bj) - (aj|bi)| for every (a, b)
     const double *bound_ab;
     const double *bound_ss;
+    int ss_any;          // 1: some bound_ss entry is non-zero (else every same-spin double is zero)
     double hbound;       // |<D'|H|D>| <= hbound for every pair of determinants
 };
 
@@ -367,6 +368,7 @@ struct BucketOut {
     // between two passes belong to both): a target outside needs no row-map load
     unsigned long long row_lo, row_hi;
     int *status;              // bit 1: overflow list full; bit 4: an element had no bucket
+    int aa_runs;              // 1: alpha-alpha doubles by runs of sources sharing alpha (own kernel)
 };
 
 struct EmitOut {
@@ -413,10 +415,11 @@ cudaError_t launch_emit_buckets(const SysDev &d, const unsigned long long *in_ra
                                 const double *in_coef, long long n_in, const BucketOut &b,
                                 cudaStream_t st, int warps = 0);
 // weights[ha] += intermediate elements bound for alpha string ha (enumerated,
-// zeros included), over all input determinants
+// zeros included), over all input determinants; *n_runs += the number of runs
+// of consecutive inputs sharing alpha
 cudaError_t launch_row_weights(const SysDev &d, const unsigned long long *in_rank,
                                const double *in_coef, long long n_in, double eps_elem,
-                               unsigned long long *weights, cudaStream_t st);
+                               unsigned long long *weights, unsigned long long *n_runs, cudaStream_t st);
 cudaError_t launch_debug_excitations(const SysDev &d, const unsigned long long *in_rank,
                                      long long n_in, long long *src, unsigned long long *tgt,
                                      double *elem, cudaStream_t st);

@@ -165,12 +165,12 @@ void log_step(const sfci_step_info &s) {
                  "\"n_emitted\": %lld, \"n_psi\": %lld, \"ms_step\": %.4f, \"ms_sigma\": %.4f, "
                  "\"ms_emit\": %.4f, \"ms_merge\": %.4f, \"ms_plan\": %.4f, \"ms_topk\": %.4f, "
                  "\"n_passes\": %d, \"redo\": %d, \"bucket_redo\": %d, \"n_overflow\": %lld, "
-                 "\"sigma_gbs_32B_per_element\": %.3f}\n",
+                 "\"n_alpha_runs\": %lld, \"sigma_gbs_32B_per_element\": %.3f}\n",
                  s.iter, s.cycle, s.index, s.cycle_end, s.converged, s.breakdown, s.lambda_min, s.a, s.b,
                  s.u_norm, (long long)s.n_in, (long long)s.n_sigma, (long long)s.n_kept,
                  (long long)s.n_elements, (long long)s.n_emitted, (long long)s.n_psi, s.ms_step, s.ms_sigma,
                  s.ms_emit, s.ms_merge, s.ms_plan, s.ms_topk, s.n_passes, s.redo, s.bucket_redo,
-                 (long long)s.n_overflow, gbs);
+                 (long long)s.n_overflow, (long long)s.n_alpha_runs, gbs);
     std::fclose(f);
 }
 
@@ -246,6 +246,7 @@ struct sfci_lanczos {
     int *lock_w = nullptr;
     unsigned long long *nread_w = nullptr;  // device word: intermediate elements merged
     long long n_emitted = 0;            // of the last sigma (host copy)
+    unsigned long long alpha_runs = 0;  // runs of inputs sharing alpha (last sigma's plan)
     double *dmin = nullptr;             // device word: min |kept|
     int n_passes = 0, nb_log2 = 0;
 };
@@ -378,7 +379,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
     sfci_status r;
     Buckets bk{};
     bk.cb = d.cb;
-    unsigned long long B = 0;
+    unsigned long long B = 0, runs = 0;
     unsigned hash_cap = 0;
     unsigned long long total_cap = 0;
     if (row_mode) {
@@ -388,7 +389,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         const unsigned long long nrows = d.ca;
         const unsigned long long Pb = std::max<unsigned long long>(2, (unsigned long long)per_bucket);
         const unsigned long long T = (unsigned long long)(E / (double)(Pb / 2)) + 2;  // windows
-        if ((r = ensure(z->weights, nrows * 8, z->st, "row weights", 1.5))) return r;
+        if ((r = ensure(z->weights, (nrows + 1) * 8, z->st, "row weights", 1.5))) return r;
         if ((r = ensure(z->rowmap, nrows * 8, z->st, "row map", 1.5))) return r;
         if ((r = ensure(z->wpre, (nrows + 1) * 8, z->st, "row offsets", 1.5))) return r;
         if ((r = ensure(z->ptl, T * 4, z->st, "plan windows", 1.5))) return r;
@@ -396,9 +397,11 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         if ((r = ensure(z->pbstart, (T + 1) * 8, z->st, "plan window offsets", 1.5))) return r;
         if ((r = ensure(z->scan_ws, scan_ws_bytes((long long)std::max(T, nrows) + 1), z->st, "scan workspace", 1.5)))
             return r;
-        SFCI_CUDA(cudaMemsetAsync(z->weights.p, 0, nrows * 8, z->st));
+        // weights[nrows]: runs of inputs sharing alpha
+        SFCI_CUDA(cudaMemsetAsync(z->weights.p, 0, (nrows + 1) * 8, z->st));
         SFCI_CUDA(launch_row_weights(d, z->wr[i], z->wc[i], n_in, z->p.eps_element,
-                                     static_cast<unsigned long long *>(z->weights.p), z->st));
+                                     static_cast<unsigned long long *>(z->weights.p),
+                                     static_cast<unsigned long long *>(z->weights.p) + nrows, z->st));
         auto *w = P<unsigned long long>(z->weights);
         SFCI_CUDA(exclusive_scan(static_cast<const unsigned long long *>(w), (long long)nrows,
                                  P<unsigned long long>(z->wpre), z->scan_ws.p, z->st));
@@ -408,6 +411,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         SFCI_CUDA(exclusive_scan(static_cast<const unsigned *>(P<unsigned>(z->pth)), (long long)T,
                                  P<unsigned long long>(z->pbstart), z->scan_ws.p, z->st));
         SFCI_CUDA(cudaMemcpyAsync(&B, P<unsigned long long>(z->pbstart) + T, 8, cudaMemcpyDeviceToHost, z->st));
+        SFCI_CUDA(cudaMemcpyAsync(&runs, w + nrows, 8, cudaMemcpyDeviceToHost, z->st));
         SFCI_CUDA(cudaStreamSynchronize(z->st));
         if (B >= (1ull << 31)) {
             set_error("too many merge buckets");
@@ -615,6 +619,7 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
         z->held_gb = held / 1e9;
         z->regions_gb = (double)total_cap * sizeof(Slot) / 1e9;
         z->n_passes = npass;
+        z->alpha_runs = runs;
         z->nb_log2 = 0;
         while ((1ull << z->nb_log2) < B) ++z->nb_log2;
         z->ms_emit = z->ms_merge = 0.0;
@@ -662,6 +667,10 @@ sfci_status bucketed_sigma(sfci_lanczos *z, int i, double *tau_io, unsigned long
                 bo.row_hi = lim[1] > 0 ? lim[1] - 1 : 0ull;
             }
             bo.status = z->mstatus;
+            // alpha-alpha doubles by runs of sources sharing alpha when a pass
+            // leaves rows for others (its queue skips them) or runs average two
+            // sources or more (row reads and reservations shared); else inline
+            bo.aa_runs = !(lo == 0 && (unsigned long long)hi >= B) || (runs > 0 && (unsigned long long)n_in >= 2 * runs);
             SFCI_CUDA(cudaEventRecord(z->evp[0], z->st));
             SFCI_CUDA(launch_emit_buckets(d, z->wr[i], z->wc[i], n_in, bo, z->st, z->p.emit_warps));
             SFCI_CUDA(cudaEventRecord(z->evp[1], z->st));
@@ -1025,6 +1034,7 @@ sfci_status sfci_lanczos_step(sfci_lanczos *z, sfci_step_info *info) {
         info->regions_gb = z->regions_gb;
         info->free_gb = z->free_gb + z->held_gb;
         info->n_overflow = z->ovf_used;
+        info->n_alpha_runs = (long long)z->alpha_runs;
         info->ms_alloc = z->ms_alloc;
         info->n_buckets_log2 = z->nb_log2;
         info->n_elements = n_in * (d.n_conn + 1);
