@@ -39,11 +39,12 @@ UNIT = "connected elements/s"
 BYTES_PER_ELEMENT = 32  # 16 B intermediate element written + 16 B read back by the merge
 # DRAM bytes per connected element that ncu measured for emit_kernel + merge_kernel
 # together (dram__bytes_read.sum + dram__bytes_write.sum of one launch each on the same
-# workload at N_d = 5e3, 1.5362e8 elements, one pass); scaled by the elements of a step
-MEASURED_DRAM_BYTES_PER_ELEMENT = (0.053608 + 2.438130 + 2.467469 + 0.004204) * 1e9 / 1.5362e8
+# workload at N_d = 5e3, 1.5362e8 elements, one pass, every excitation class in the emit
+# kernel); scaled by the elements of a step
+MEASURED_DRAM_BYTES_PER_ELEMENT = (0.051976 + 2.438313 + 2.467443 + 0.004534) * 1e9 / 1.5362e8
 # warp instructions per connected element (smsp__inst_executed.sum of the same captures) and
 # the issue ceiling: 152 SMs x 4 schedulers x one warp instruction per clock at 2070 MHz
-MEASURED_WARP_INST_PER_ELEMENT = {"emit_kernel": 1165891164 / 1.5362e8, "merge_kernel": 1999301422 / 1.5362e8}
+MEASURED_WARP_INST_PER_ELEMENT = {"emit": 1168350231 / 1.5362e8, "merge_kernel": 1999586496 / 1.5362e8}
 ISSUE_PEAK_WARP_INST_PER_S = 152 * 4 * 2.07e9
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -68,6 +69,9 @@ def parse():
                    help="intermediate elements per merge bucket (0 = automatic)")
     p.add_argument("--table-capacity", type=int, default=0,
                    help="merge-table slots (0 = sized by the solver)")
+    p.add_argument("--mem-budget-gb", type=float, default=0.0,
+                   help="device memory the sigma passes may use (0 = what is free); a small budget "
+                        "gives a small case with several passes, for profiling")
     p.add_argument("--emit-warps", type=int, default=0,
                    help="warps per CTA of the element generator (0 = 8)")
     p.add_argument("--workload", default="sfci", choices=["sfci", "scan"],
@@ -540,7 +544,7 @@ def run_ours(a):
     stream = torch.cuda.current_stream()
     lz = sf.Lanczos(gsys, np.array([0], dtype=np.uint64), np.array([1.0]), a.nkeep, a.nlanczos,
                     table_capacity=a.table_capacity, bucket_elems=a.bucket_elems, stream=stream,
-                    emit_warps=a.emit_warps)
+                    emit_warps=a.emit_warps, mem_budget=int(a.mem_budget_gb * 1e9))
 
     def brief(i):
         return {k: i[k] for k in ("n_in", "n_sigma", "n_passes", "ms_plan", "ms_emit", "ms_merge",
@@ -584,7 +588,7 @@ def run_ours(a):
                 "frac": achieved / hbm, "traffic": MEASURED_DRAM_BYTES_PER_ELEMENT * el_per_launch,
                 "traffic_note": "bytes per launch: ncu DRAM bytes per element of emit_kernel + "
                                 "merge_kernel (N_d = 5e3 capture, one pass) x elements per launch",
-                "kernel": "sigma stage: emit_kernel + merge_kernel",
+                "kernel": "sigma stage: emit (emit_kernel, emit_aa_kernel) + merge_kernel",
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "model": f"{BYTES_PER_ELEMENT} B per connected element (16 B written by emit, "
                          f"16 B read by merge)",
@@ -598,13 +602,14 @@ def run_ours(a):
                 "sigma_share_of_step": sum(i["ms_sigma"] for i in infos) / ms,
                 # the kernels are bound by instruction issue and latency, not by DRAM: the
                 # issue-slot view, with warp instructions per element from the N_d = 5e3
-                # captures (at N_d = 1e6 entries repeat more, so the merge streams out fewer
-                # entries per element and this overstates its count)
+                # one-pass captures (at N_d = 1e6 entries repeat more, so the merge streams
+                # out fewer entries per element and this overstates its count; the emit stage
+                # there is emit_kernel plus emit_aa_kernel over three passes)
                 "issue": {kname: {"warp_inst_per_element": ipe,
                                   "achieved_warp_inst_per_s": ipe * el_per_launch / (ms_k * 1e-3),
                                   "peak_warp_inst_per_s": ISSUE_PEAK_WARP_INST_PER_S,
                                   "frac": ipe * el_per_launch / (ms_k * 1e-3) / ISSUE_PEAK_WARP_INST_PER_S}
-                          for kname, ipe, ms_k in (("emit_kernel", MEASURED_WARP_INST_PER_ELEMENT["emit_kernel"], ms_emit),
+                          for kname, ipe, ms_k in (("emit", MEASURED_WARP_INST_PER_ELEMENT["emit"], ms_emit),
                                                    ("merge_kernel", MEASURED_WARP_INST_PER_ELEMENT["merge_kernel"], ms_merge))}}
 
     # end to end through the public API with host buffers, chained: each step
