@@ -31,6 +31,7 @@
 // row has at most kHopBins buckets reserve their places per bucket once for
 // the whole hop.
 #include <algorithm>
+#include <type_traits>
 
 #include "sfci_internal.cuh"
 
@@ -50,15 +51,23 @@ __host__ __device__ inline size_t block_smem(const SysDev &d) {
 // buckets reserve their places per bucket once per hop (bins below).
 constexpr int kHopBins = 32;
 
-// per warp: overflow chunk cursor (2 u64), rankA1, rankB1 (u64), prefix sums
-// (3 ks u64), offA1, offB1, mixB (u32), the hop's bins (4 x kHopBins u32), hopX
-// (u16 per alpha hop), yoff (u16 per beta hop), occupation lists (256 B)
-__host__ __device__ inline size_t warp_smem(const SysDev &d) {
-    return align16(16 + size_t(d.sa) * 14 + size_t(d.sb) * 18 + size_t(3 * d.ks) * 8 + size_t(kHopBins) * 16 + 256);
+// per warp: overflow chunk cursor (2 u64), prefix sums (3 ks u64), rankA1,
+// rankB1 (u32 when every string index fits 32 bits, else u64), offA1, offB1,
+// mixB (u32), the hop's bins (4 x kHopBins u32), hopX (u16 per alpha hop), yoff
+// (u16 per beta hop), occupation lists (256 B).  The 32-bit tables keep a CTA of
+// eight warps small enough that four CTAs leave the SM 92 KB of L1 instead of
+// 60 KB (the integral rows and the row map are read through it; measured).
+__host__ __device__ inline size_t warp_smem(const SysDev &d, bool narrow = false) {
+    const size_t r = narrow ? 4 : 8;
+    return align16(16 + size_t(d.sa) * (r + 6) + size_t(d.sb) * (r + 10) + size_t(3 * d.ks) * 8 +
+                   size_t(kHopBins) * 16 + 256);
 }
 
-inline size_t emit_smem_bytes_w(const SysDev &d, int warps) {
-    return block_smem(d) + size_t(warps) * warp_smem(d);
+// string indices below 2^32 on both spins: 32-bit single tables
+__host__ __device__ inline bool narrow_ranks(const SysDev &d) { return (d.ca >> 32) == 0 && (d.cb >> 32) == 0; }
+
+inline size_t emit_smem_bytes_w(const SysDev &d, int warps, bool narrow = false) {
+    return block_smem(d) + size_t(warps) * warp_smem(d, narrow);
 }
 
 // single element h_ai + sum_{k occ alpha} (ai|kk) + sum_{k occ beta} (ai|kk)
@@ -417,10 +426,11 @@ __device__ __forceinline__ unsigned long long pair_rank(unsigned long long rem, 
            pre[2 * ks + (M - 2)] - pre[2 * ks + q2];
 }
 
-template <int kMode>
+template <int kMode, bool kNarrow = false>
 __global__ void __launch_bounds__(kEmitThreads, 4)
 emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             const double *__restrict__ in_coef, long long n_in, const EmitOut o) {
+    using RankT = typename std::conditional<kNarrow, unsigned, unsigned long long>::type;
     extern __shared__ __align__(16) unsigned char sm[];
     const int n = d.n, ks = d.ks;
     unsigned long long *bt = reinterpret_cast<unsigned long long *>(sm);
@@ -430,12 +440,12 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *wb = sm + block_smem(d) + size_t(warp) * warp_smem(d);
+    unsigned char *wb = sm + block_smem(d) + size_t(warp) * warp_smem(d, kNarrow);
     unsigned long long *ocur = reinterpret_cast<unsigned long long *>(wb);  // overflow chunk cursor
-    unsigned long long *rankA1 = ocur + 2;
-    unsigned long long *rankB1 = rankA1 + d.sa;
-    unsigned long long *pre = rankB1 + d.sb;  // prefix sums A0 | A1 | A2, ks each
-    unsigned *offA1 = reinterpret_cast<unsigned *>(pre + 3 * ks);
+    unsigned long long *pre = ocur + 2;  // prefix sums A0 | A1 | A2, ks each
+    RankT *rankA1 = reinterpret_cast<RankT *>(pre + 3 * ks);
+    RankT *rankB1 = rankA1 + d.sa;
+    unsigned *offA1 = reinterpret_cast<unsigned *>(rankB1 + d.sb);
     unsigned *offB1 = offA1 + d.sa;
     unsigned *mixB = offB1 + d.sb;  // top 32 bits of mix64 of each beta hop's index (its bucket in a split row)
     unsigned *hcnt = mixB + d.sb;   // per bucket of the current alpha hop's row: elements,
@@ -476,16 +486,16 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
             const int io = x / d.va, iv = x - io * d.va;
             const int i = occA[io], a = virA[iv];
             const unsigned sg = parity64(alpha & between_mask(i, a));
-            rankA1[x] = string_rank(alpha ^ (1ull << i) ^ (1ull << a), bt, ks);
+            rankA1[x] = (RankT)string_rank(alpha ^ (1ull << i) ^ (1ull << a), bt, ks);
             offA1[x] = unsigned((a * n + i) * n2) | (sg << 31);
         }
         for (int y = lane; y < d.sb; y += 32) {
             const int jo = y / d.vb, jv = y - jo * d.vb;
             const int j = occB[jo], b = virB[jv];
             const unsigned sg = parity64(beta & between_mask(j, b));
-            rankB1[y] = string_rank(beta ^ (1ull << j) ^ (1ull << b), bt, ks);
+            rankB1[y] = (RankT)string_rank(beta ^ (1ull << j) ^ (1ull << b), bt, ks);
             offB1[y] = unsigned(b * n + j) | (sg << 31);
-            if (kMode == kModeBucket) mixB[y] = (unsigned)(mix64(rankB1[y]) >> 32);
+            if (kMode == kModeBucket) mixB[y] = (unsigned)(mix64((unsigned long long)rankB1[y]) >> 32);
         }
         __syncwarp();
         // alpha hops whose target row can hold buckets of this pass (every hop
@@ -1069,24 +1079,23 @@ int device_sms() {
 
 // warps per CTA: the requested count (0: 8), lowered until the CTA's shared
 // memory fits the device's per-block limit
-int emit_warps_for(const SysDev &d, int want) {
+int emit_warps_for(const SysDev &d, int want, bool narrow = false) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int w = want > 0 && want < kEmitWarps ? want : kEmitWarps;
-    while (w > 1 && emit_smem_bytes_w(d, w) > (size_t)optin) --w;
-    return emit_smem_bytes_w(d, w) <= (size_t)optin ? w : 0;
+    while (w > 1 && emit_smem_bytes_w(d, w, narrow) > (size_t)optin) --w;
+    return emit_smem_bytes_w(d, w, narrow) <= (size_t)optin ? w : 0;
 }
 
-template <int kMode>
-cudaError_t launch_emit_impl(const SysDev &d, const unsigned long long *in_rank,
-                             const double *in_coef, long long n_in, const EmitOut &o,
-                             cudaStream_t st, int want_warps = 0) {
-    if (n_in <= 0) return cudaSuccess;
-    const int warps = emit_warps_for(d, want_warps);
+template <int kMode, bool kNarrow>
+cudaError_t launch_emit_k(const SysDev &d, const unsigned long long *in_rank,
+                          const double *in_coef, long long n_in, const EmitOut &o,
+                          cudaStream_t st, int want_warps) {
+    const int warps = emit_warps_for(d, want_warps, kNarrow);
     if (warps < 1) return cudaErrorInvalidConfiguration;  // one warp's tables exceed shared memory
-    const size_t smem = emit_smem_bytes_w(d, warps);
-    auto kern = emit_kernel<kMode>;
+    const size_t smem = emit_smem_bytes_w(d, warps, kNarrow);
+    auto kern = emit_kernel<kMode, kNarrow>;
     cudaError_t e = allow_max_smem(kern, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -1099,6 +1108,18 @@ cudaError_t launch_emit_impl(const SysDev &d, const unsigned long long *in_rank,
     count_launch();
     kern<<<(unsigned)grid, warps * 32, smem, st>>>(d, in_rank, in_coef, n_in, o);
     return cudaGetLastError();
+}
+
+// bucket mode takes the 32-bit single tables when every string index fits
+template <int kMode>
+cudaError_t launch_emit_impl(const SysDev &d, const unsigned long long *in_rank,
+                             const double *in_coef, long long n_in, const EmitOut &o,
+                             cudaStream_t st, int want_warps = 0) {
+    if (n_in <= 0) return cudaSuccess;
+    if constexpr (kMode == kModeBucket) {
+        if (narrow_ranks(d)) return launch_emit_k<kMode, true>(d, in_rank, in_coef, n_in, o, st, want_warps);
+    }
+    return launch_emit_k<kMode, false>(d, in_rank, in_coef, n_in, o, st, want_warps);
 }
 
 }  // namespace
