@@ -196,12 +196,34 @@ __device__ __forceinline__ void overflow_append(const BucketOut &B, bool of, con
     else atomicOr(B.status, 2);
 }
 
+// A row split into several buckets (a heavy row) gives them equal regions, so
+// within one pass the region of its bucket b >= b0 starts at s0 + (b - b0) c4
+// (units of 4 slots; b0 = the row's first bucket in the pass).  c4 == 0: not
+// such a row (one bucket, or hash mode).  Only for rows with buckets in the pass.
+struct RowRegion {
+    unsigned b0, s0, c4;
+};
+
+// bucket of a target whose alpha row is known ahead (first bucket and bucket
+// count of the row read once): ns == ~0 means hash mode (no row map)
+struct RowCtx {
+    unsigned first, ns;
+};
+
+__device__ __forceinline__ RowRegion row_region(const BucketOut &B, RowCtx rc) {
+    if (rc.ns == 0xffffffffu || rc.ns < 2u) return RowRegion{0u, 0u, 0u};
+    const unsigned b0 = rc.first > B.lo ? rc.first : B.lo;
+    const unsigned s0 = __ldg(&B.start4[b0]);
+    return RowRegion{b0, s0, __ldg(&B.start4[b0 + 1]) - s0};
+}
+
 // Up to kU elements per lane (ok[k]) are appended to their buckets: the lanes
 // of the warp that share a bucket reserve their slots with one atomic, issued
-// for all k before any result is used, and write one run.
+// for all k before any result is used, and write one run.  With rr.c4 set,
+// every element's bucket belongs to rr's row and its region is computed, not read.
 __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, const unsigned *bk,
                                             const unsigned long long *tg, const double *v,
-                                            unsigned long long *cur) {
+                                            unsigned long long *cur, RowRegion rr = RowRegion{0u, 0u, 0u}) {
     const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
     unsigned peers[kU], base[kU];
 #pragma unroll
@@ -219,20 +241,20 @@ __device__ __forceinline__ void warp_append(const BucketOut &B, const bool *ok, 
         const ulonglong2 sl = make_ulonglong2(tg[k], (unsigned long long)__double_as_longlong(v[k]));
         if (ok[k]) {
             const unsigned pos = base[k] + __popc(peers[k] & lt);
-            const unsigned long long o0 = (unsigned long long)__ldg(&B.start4[bk[k]]) << 2;
-            const unsigned long long o1 = (unsigned long long)__ldg(&B.start4[bk[k] + 1]) << 2;
-            if (pos < o1 - o0) __stcs(reinterpret_cast<ulonglong2 *>(B.elem) + o0 + pos, sl);  // streamed: read once by the merge
+            unsigned long long o0, room;
+            if (rr.c4) {
+                o0 = (unsigned long long)(rr.s0 + (bk[k] - rr.b0) * rr.c4) << 2;
+                room = (unsigned long long)rr.c4 << 2;
+            } else {
+                o0 = (unsigned long long)__ldg(&B.start4[bk[k]]) << 2;
+                room = ((unsigned long long)__ldg(&B.start4[bk[k] + 1]) << 2) - o0;
+            }
+            if (pos < room) __stcs(reinterpret_cast<ulonglong2 *>(B.elem) + o0 + pos, sl);  // streamed: read once by the merge
             else of = true;
         }
         overflow_append(B, of, sl, cur);
     }
 }
-
-// bucket of a target whose alpha row is known ahead (first bucket and bucket
-// count of the row read once): ns == ~0 means hash mode (no row map)
-struct RowCtx {
-    unsigned first, ns;
-};
 
 __device__ __forceinline__ RowCtx row_ctx(const BucketOut &B, unsigned long long ha) {
     if (!B.bk.rowmap) return RowCtx{0u, 0xffffffffu};
@@ -344,7 +366,7 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
                                            const unsigned *bk, const double *e, const long long *di,
                                            long long s, double c, unsigned long long cb,
                                            unsigned &inserted, unsigned long long *cur,
-                                           long long single = -1) {
+                                           long long single = -1, RowRegion rr = RowRegion{0u, 0u, 0u}) {
     if constexpr (kMode == kModeDebug) {
 #pragma unroll
         for (int k = 0; k < kU; ++k)
@@ -382,7 +404,7 @@ __device__ __forceinline__ void emit_round(const EmitOut &o, const bool *want,
         for (int k = 0; k < kU; ++k) any |= ok[k];
         if (!__any_sync(kFull, any)) return;  // nothing of this pass in the round
         if (single >= 0) single_append(o.b, (unsigned)single, ok, tg, v, cur);
-        else warp_append(o.b, ok, bk, tg, v, cur);
+        else warp_append(o.b, ok, bk, tg, v, cur, rr);
     }
 }
 
@@ -584,7 +606,8 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     want[k] = true, ha[k] = hA, hb[k] = rankB1[y], di[k] = off + y;
                     e[k] = flip(F, offB1[y] >> 31);
                 }
-                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, self_single);
+                emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, self_single,
+                                  row_region(o.b, rs));  // (the own row is in this pass here)
             }
         }
         off += d.sb;
@@ -633,7 +656,8 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                                               : __dsub_rn(__ldg(&g[x1]), __ldg(&g[x2]));
                         e[k] = flip(gd, unsigned(s1 ^ s2));
                     }
-                    emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, spin ? self_single : -1);
+                    emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, spin ? self_single : -1,
+                                      spin ? row_region(o.b, rs) : RowRegion{0u, 0u, 0u});
                 }
                 __syncwarp();
             }
@@ -697,6 +721,9 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                     }
                     __syncwarp();  // the bins are reused by the next hop
                 } else {
+                    // a row split more ways than there are bins (or hash mode): per
+                    // round reservations, regions computed from the row's first one
+                    const RowRegion rhop = row_region(o.b, rc);
                     for (int y0 = 0; y0 < d.sb; y0 += 32 * kU) {
                         SFCI_CLEAR();
 #pragma unroll
@@ -711,7 +738,7 @@ emit_kernel(const SysDev d, const unsigned long long *__restrict__ in_rank,
                             want[k] = true, ha[k] = ra, hb[k] = hbv;
                             e[k] = flip(gv, (oa ^ ob) >> 31);
                         }
-                        emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, -1);
+                        emit_round<kMode>(o, want, ha, hb, bk, e, di, s, c, cb, inserted, ocur, -1, rhop);
                     }
                 }
             }
