@@ -371,7 +371,7 @@ merge_kernel(MergeArgs A) {
                                 break;
                             }
                         }
-                        h = (h + 1) & (kSlots - 1);
+                        h = (h + (unsigned)probe + 1u) & (kSlots - 1);  // triangular steps: every slot once
                     }
                 }
                 // newly occupied slots: one list reservation per warp
@@ -421,7 +421,7 @@ merge_kernel(MergeArgs A) {
                     break;
                 }
                 if (c == kEmpty) break;
-                h = (h + 1) & (kSlots - 1);
+                h = (h + (unsigned)q + 1u) & (kSlots - 1);
             }
             double sv = found >= 0 ? from_fixed(acc_lo[found], acc_hi[found], S) : 0.0;
             if (screen && abs_bits(sv) < eps_bits) sv = 0.0;  // screened entries count as absent
