@@ -41,10 +41,10 @@ BYTES_PER_ELEMENT = 32  # 16 B intermediate element written + 16 B read back by 
 # together (dram__bytes_read.sum + dram__bytes_write.sum of one launch each on the same
 # workload at N_d = 5e3, 1.5362e8 elements, one pass, every excitation class in the emit
 # kernel); scaled by the elements of a step
-MEASURED_DRAM_BYTES_PER_ELEMENT = (0.051976 + 2.438313 + 2.467443 + 0.004534) * 1e9 / 1.5362e8
+MEASURED_DRAM_BYTES_PER_ELEMENT = (0.052011 + 2.438096 + 2.467282 + 0.004709) * 1e9 / 1.5362e8
 # warp instructions per connected element (smsp__inst_executed.sum of the same captures) and
 # the issue ceiling: 152 SMs x 4 schedulers x one warp instruction per clock at 2070 MHz
-MEASURED_WARP_INST_PER_ELEMENT = {"emit": 1168350231 / 1.5362e8, "merge_kernel": 1999586496 / 1.5362e8}
+MEASURED_WARP_INST_PER_ELEMENT = {"emit": 1154000833 / 1.5362e8, "merge_kernel": 1938576001 / 1.5362e8}
 ISSUE_PEAK_WARP_INST_PER_S = 152 * 4 * 2.07e9
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
