@@ -315,9 +315,12 @@ merge_kernel(MergeArgs A) {
         const ulonglong2 *ovs = reinterpret_cast<const ulonglong2 *>(A.ovf_sorted) + o0;
         const unsigned total = n_main + (unsigned)(o1 - o0);
         if (tid == 0) s_nread += total;
-        // keys repeat a lot in a bucket past its region or holding more
-        // elements than table slots: lanes sharing a key are summed first
-        const bool hot = o1 > o0 || total > (unsigned)kSlots;
+        // keys repeat a lot in a bucket past its region or holding more than
+        // four elements per table slot: there the lanes sharing a key are
+        // summed first (one table update per key and round); elsewhere a
+        // round of 32 records rarely repeats a key and the grouping costs more
+        // than it saves (measured)
+        const bool hot = o1 > o0 || total > 4u * (unsigned)kSlots;
         for (unsigned e0 = 0; e0 < total; e0 += kMT * kPre) {
             ulonglong2 x[kPre];
 #pragma unroll
