@@ -46,6 +46,8 @@ MEASURED_DRAM_BYTES_PER_ELEMENT = (0.052011 + 2.438096 + 2.467282 + 0.004709) * 
 # the issue ceiling: 152 SMs x 4 schedulers x one warp instruction per clock at 2070 MHz
 MEASURED_WARP_INST_PER_ELEMENT = {"emit": 1154000833 / 1.5362e8, "merge_kernel": 1938576001 / 1.5362e8}
 ISSUE_PEAK_WARP_INST_PER_S = 152 * 4 * 2.07e9
+# the constants above were captured before merge_kernel's key-grouping threshold changed
+TRAFFIC_STALE = True
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -585,9 +587,15 @@ def run_ours(a):
     hbm, peak_kind = peaks()
     achieved = BYTES_PER_ELEMENT * el_per_launch / (ms_sig * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": MEASURED_DRAM_BYTES_PER_ELEMENT * el_per_launch,
+                "frac": achieved / hbm,
+                # null: merge_kernel changed (its key-grouping threshold) after the last
+                # capture; that capture's figure, which the change does not touch (the same
+                # records are read), is kept below for reference
+                "traffic": None if TRAFFIC_STALE else MEASURED_DRAM_BYTES_PER_ELEMENT * el_per_launch,
+                "traffic_last_capture": MEASURED_DRAM_BYTES_PER_ELEMENT * el_per_launch,
                 "traffic_note": "bytes per launch: ncu DRAM bytes per element of emit_kernel + "
-                                "merge_kernel (N_d = 5e3 capture, one pass) x elements per launch",
+                                "merge_kernel (N_d = 5e3 capture, one pass) x elements per launch; "
+                                "null while a kernel has changed since that capture",
                 "kernel": "sigma stage: emit (emit_kernel, emit_aa_kernel) + merge_kernel",
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "model": f"{BYTES_PER_ELEMENT} B per connected element (16 B written by emit, "
@@ -600,6 +608,9 @@ def run_ours(a):
                 "elements_per_launch": el_per_launch,
                 "nonzero_elements_per_launch": statistics.mean(i["n_emitted"] for i in infos),
                 "sigma_share_of_step": sum(i["ms_sigma"] for i in infos) / ms,
+                "issue_note": "merge_kernel's instructions per element were captured before its "
+                              "key-grouping threshold changed (fewer grouped buckets: fewer "
+                              "instructions now)" if TRAFFIC_STALE else "",
                 # the kernels are bound by instruction issue and latency, not by DRAM: the
                 # issue-slot view, with warp instructions per element from the N_d = 5e3
                 # one-pass captures (at N_d = 1e6 entries repeat more, so the merge streams
