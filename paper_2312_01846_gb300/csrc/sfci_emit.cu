@@ -29,7 +29,15 @@
 // The lanes of the warp stride over the excitations of each class, one element
 // per lane per round; the opposite-spin doubles of an alpha hop whose target
 // row has at most kHopBins buckets reserve their places per bucket once for
-// the whole hop.
+// the whole hop, and reservations into a row split further compute its
+// buckets' region offsets from the first one (equal regions).
+//
+// In bucket mode the alpha-alpha doubles can go by runs instead
+// (emit_aa_kernel): the sources sharing an alpha string are consecutive, so a
+// warp takes a window of 32 sources, computes each run's alpha-alpha
+// excitations once and pairs the live ones with the run's beta strings.  The
+// host picks that path when a pass leaves rows to others or the runs average
+// two sources or more.
 #include <algorithm>
 #include <type_traits>
 
