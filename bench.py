@@ -435,7 +435,7 @@ def screen_study(sf, d, nkeep, n_lanczos, steps, stream, eps_list):
 
 
 def solver_row(sf, d, name, nkeep, n_lanczos, warmup, steps, stream, note):
-    """One SURVEY-style measurement row: the solver from the aufbau determinant,
+    """One workload row of the bench line: the solver from the aufbau determinant,
     `warmup` untimed steps, then `steps` timed with CUDA events on the solver's
     stream.  Enumerated and generated (non-zero) elements per second, Lanczos
     steps per second, mean sigma time and the cycle-end energies."""
