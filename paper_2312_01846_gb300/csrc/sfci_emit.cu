@@ -809,10 +809,10 @@ __host__ __device__ inline size_t aa_warp_smem(const SysDev &d) {
 // coefficient.  A work unit is a window of 32 consecutive sources and one of
 // n_groups slices of the occupied pairs (i, j) (several slices when the
 // windows alone are too few to fill the GPU); the warp splits the window into
-// its runs.  For a run of length L, the warp first takes the
-// excitations (i, j) -> (a, b) one per lane: target row, its buckets (one
-// row-map read) and the element; those whose row can hold buckets of this
-// pass and whose element is not zero join a queue.  Rounds of 32 (excitation,
+// its runs.  For a run of length L, the warp first takes the excitations
+// (i, j) -> (a, b) one per lane: target row, its buckets (one row-map read)
+// and the element; those whose row can hold buckets of this pass and whose
+// element is not zero join a queue.  Rounds of 32 (excitation,
 // source) items then leave the queue (lane t: excitation t / L, source
 // t mod L, in queue order), so a round is full whatever the share of rows in
 // the pass, and the lanes of one excitation share a row and often a bucket
